@@ -1,0 +1,172 @@
+/*
+ * psvd.h - C-ABI of the GB300-native streaming, partitioned, randomized SVD
+ * (Maulik & Mengaldo, "PyParSVD", arXiv 2108.08845).
+ *
+ * One handle holds one stream of snapshots: the current left singular vectors
+ * (modes) U (M x k, k <= K) and singular values D (k) of Algorithm 1 (Sec. 3.1).
+ * Every compute step runs in the library's own CUDA kernels for sm_103a; there is
+ * no host or library fallback.
+ *
+ * Conventions shared by all entry points
+ *   - Matrices are column-major: element (i, j) of a matrix with leading
+ *     dimension ld is at ptr[i + j*ld].  Rows are grid points (degrees of
+ *     freedom), columns are snapshots (Sec. 3.1/3.2), so each snapshot is
+ *     contiguous.
+ *   - Data pointers may be device pointers or host pointers (pageable or
+ *     pinned); the library detects which with cudaPointerGetAttributes.  Host
+ *     inputs are staged through a device buffer owned by the handle.
+ *   - Work is enqueued on the handle's CUDA stream.  Calls that return data to
+ *     the caller (psvd_get_*, psvd_parallel_qr, psvd_parallel_svd) synchronise
+ *     that stream before returning.  Calls that only consume inputs
+ *     (psvd_initialize, psvd_incorporate_data) return as soon as the work is
+ *     enqueued when the input is a device pointer; the caller must keep device
+ *     inputs alive and unmodified until the stream reaches that point.
+ *   - Ownership: the caller owns every pointer it passes; the handle owns its
+ *     modes, singular values, workspaces and random-number state.
+ *   - Errors: every int-returning call returns PSVD_OK (0), a positive warning,
+ *     or a negative error code; no exception or abort crosses the ABI.  After a
+ *     PSVD_ERR_CUDA the handle must be destroyed.
+ *   - Threading: a handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef PSVD_H
+#define PSVD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define PSVD_OK 0
+#define PSVD_WARN_RANK_DEFICIENT 1   /* a kept singular value is (numerically) zero;
+                                        its mode is set to zero (Alg. 2, Lambda_j = 0) */
+#define PSVD_WARN_NOT_CONVERGED 2    /* the small Jacobi eigen-solve hit its sweep cap;
+                                        results are those of the last sweep */
+#define PSVD_ERR_INVALID_ARG -1      /* null handle/pointer, ld < M, bad enum, ff not in (0,1] */
+#define PSVD_ERR_NOT_INITIALIZED -2  /* psvd_incorporate_data / get before psvd_initialize */
+#define PSVD_ERR_SHAPE -3            /* B > max_batch, M < K + B, K + max_batch > 192, ... */
+#define PSVD_ERR_NONFINITE -4        /* a NaN or Inf reached the small factor */
+#define PSVD_ERR_CUDA -5             /* a CUDA runtime call failed */
+#define PSVD_ERR_ALLOC -6            /* device or host allocation failed */
+#define PSVD_ERR_IO -7               /* psvd_save / psvd_load file error or bad format */
+#define PSVD_ERR_UNSUPPORTED -8      /* feature not available for this precision/shape */
+
+/* ----------------------------------------------------------------- enums */
+typedef enum {
+  PSVD_F32 = 0,  /* IEEE binary32 */
+  PSVD_BF16 = 1, /* bfloat16 (8-bit exponent, 7-bit fraction) */
+  PSVD_F64 = 2   /* IEEE binary64 (only for the small outputs) */
+} psvd_dtype;
+
+typedef enum {
+  /* "plain FP32": panel Gram and mode update on the FP32 CUDA cores with
+     compensated (float-float) accumulation and an FP64 cross-block reduction;
+     modes stored in FP32. */
+  PSVD_PREC_FP32 = 0,
+  /* tcgen05 tensor cores: snapshots in BF16, modes stored as a BF16 hi/lo pair
+     (16 significant bits), panel Gram and mode update on the tensor cores with
+     FP32 accumulation in tensor memory and an FP64 cross-block reduction. */
+  PSVD_PREC_BF16_TC = 1
+} psvd_precision;
+
+/* --------------------------------------------------------------- config */
+typedef struct {
+  int64_t M;          /* rows (grid points) of every snapshot, >= 1 */
+  int32_t K;          /* modes kept after every batch (Alg. 1 steps 3 and 5), >= 1 */
+  int32_t max_batch;  /* largest snapshot count B per call; K + max_batch <= 192 */
+  double ff;          /* forget factor in (0, 1] (Sec. 3.1): scales U*D, i.e. sigma */
+  int32_t precision;  /* psvd_precision */
+  int32_t low_rank;   /* 1: the SVD of each panel is the randomized low-rank SVD
+                         of Sec. 3.3 (range finder Y = P*Omega); 0: exact */
+  int32_t oversample; /* p: the sketch has l = K + p columns (low_rank only) */
+  int32_t power_iters;/* q: power iterations of the range finder (low_rank only) */
+  uint64_t seed;      /* Philox4x32-10 key of the Gaussian sketches */
+  void* stream;       /* cudaStream_t the handle enqueues on; NULL = default stream */
+} psvd_config;
+
+typedef struct psvd_ctx* psvd_handle;
+
+/* psvd_create: allocates a handle for config *cfg (copied).  Device memory:
+ * two M x K mode buffers (FP32, or a BF16 hi/lo pair) plus O(M) staging and
+ * O((K+max_batch)^2) workspaces.  *out is set to NULL on failure. */
+int psvd_create(psvd_handle* out, const psvd_config* cfg);
+
+/* psvd_destroy: synchronises the handle's stream and frees everything it owns.
+ * Null is a no-op. */
+void psvd_destroy(psvd_handle h);
+
+/* psvd_initialize: Algorithm 1 steps I1-I2 (Sec. 3.1) on the first batch
+ * A0 (M x B, leading dimension lda >= M, dtype PSVD_F32 or PSVD_BF16):
+ * QR of A0, SVD of R, U0 = Q U' truncated to k = min(K, B) modes.
+ * Implemented as the Gram of A0, its eigen-decomposition, and U0 = A0 V D^-1. */
+int psvd_initialize(psvd_handle h, const void* A0, int64_t lda, int32_t B, int32_t dtype);
+
+/* psvd_incorporate_data: Algorithm 1 steps 1-5 (Sec. 3.1) for one new batch
+ * A (M x B, lda >= M, B <= max_batch, M >= k + B): QR of [ff*U*D | A], SVD of
+ * its R, keep min(K, k+B) modes, U <- Q U~.  The panel is never materialised:
+ * its Gram [U|A]^T[U|A] is scaled by diag(ff*D, 1) on the small side. */
+int psvd_incorporate_data(psvd_handle h, const void* A, int64_t lda, int32_t B, int32_t dtype);
+
+/* psvd_parallel_qr: the R factor of the row-partitioned QR of Sec. 4.2 for a
+ * tall panel P (M x n, ldp >= M, n <= K + max_batch, dtype F32 or BF16), with
+ * the handle's M.  R (n x n, upper triangular, diag >= 0) is written to R_out
+ * (column-major, leading dimension n, FP64; host or device).  R is the
+ * Cholesky factor of the panel's Gram, computed in FP64 from the Gram that the
+ * update kernels use.  Returns PSVD_ERR_NONFINITE if the Gram is not positive
+ * definite. */
+int psvd_parallel_qr(psvd_handle h, const void* P, int64_t ldp, int32_t n, int32_t dtype,
+                     double* R_out);
+
+/* psvd_parallel_svd: Algorithm 2 (APMOS, Sec. 3.2) on the row blocks
+ * [part_offsets[b], part_offsets[b+1]) of A (Mtot x N, lda >= Mtot; dtype F32
+ * or BF16), part_offsets a host array of nparts+1 increasing values with
+ * part_offsets[0] = 0 and part_offsets[nparts] = Mtot; every block needs
+ * >= N rows.  Local right singular vectors (r1 kept per block), gather of
+ * W = [V~^1 S~^1, ...], SVD of W (r2 kept), then U~^b_j = A^b X~_j / L~_j.
+ * Outputs: U_out (Mtot x r2, FP32, ldu >= Mtot), L_out (r2, FP64), host or
+ * device.  N <= 192, r1 <= N, r2 <= min(N, r1*nparts). */
+int psvd_parallel_svd(psvd_handle h, const void* A, int64_t lda, const int64_t* part_offsets,
+                      int32_t nparts, int32_t N, int32_t dtype, int32_t r1, int32_t r2,
+                      float* U_out, int64_t ldu, double* L_out);
+
+/* psvd_get_modes: copies the current modes (M x k, FP32; a BF16 hi/lo pair is
+ * summed exactly) into U_out (ldu >= M, host or device). */
+int psvd_get_modes(psvd_handle h, float* U_out, int64_t ldu);
+
+/* psvd_get_singular_values: copies the current k singular values (descending,
+ * FP64) into s_out (host or device). */
+int psvd_get_singular_values(psvd_handle h, double* s_out);
+
+/* psvd_num_modes: current mode count k (0 before psvd_initialize), or < 0. */
+int psvd_num_modes(psvd_handle h);
+
+/* psvd_save: writes (config, iteration, k, D, U as FP32, Philox counter) to a
+ * binary file; psvd_load recreates a handle from it on the given stream.  A
+ * loaded handle continues bit-identically to the one that was saved. */
+int psvd_save(psvd_handle h, const char* path);
+int psvd_load(psvd_handle* out, const char* path, void* stream);
+
+/* psvd_gaussian_sketch: the Philox4x32-10 Gaussian test matrix of Sec. 3.3
+ * used by the randomized path: out (rows x cols, column-major, ld = rows,
+ * FP32, device) gets variates i + j*rows of stream (seed, stream_id), each a
+ * Box-Muller transform computed in FP64 from IEEE-exact operations and rounded
+ * to FP32.  Enqueued on `stream` (cudaStream_t, NULL = default). */
+int psvd_gaussian_sketch(uint64_t seed, uint64_t stream_id, int64_t rows, int64_t cols,
+                         float* out, void* stream);
+
+/* psvd_status_string: static description of a status code. */
+const char* psvd_status_string(int status);
+
+/* psvd_last_info: diagnostics of the most recent update (synchronises): info4[0]
+ * and info4[1] are the Jacobi sweeps of the two FP32 stages of the small
+ * eigen-solve, info4[2] the accumulated status bits since psvd_initialize
+ * (1 rank deficient, 2 not converged, 4 non-finite), info4[3] the kept mode
+ * count.  info4 is a host int32[4]. */
+int psvd_last_info(psvd_handle h, int32_t* info4);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PSVD_H */

@@ -1,0 +1,509 @@
+// C-ABI entry points (include/psvd.h): handle lifetime, argument checks, and the
+// launch sequence of the per-batch update of Algorithm 1 (Sec. 3.1):
+//
+//   Gram of [U | A] over row chunks  ->  FP64 reduction + diag(ff D, 1) scaling
+//   ->  eigen-decomposition of the small (K+B)^2 matrix (FP32 Jacobi + FP64
+//   refinement)  ->  T = S V diag(1/sigma)  ->  U_new = [U | A] T.
+//
+// All device work is enqueued on the handle's stream; nothing runs on the host
+// but argument checks, pointer classification and launch configuration.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "psvd_internal.cuh"
+#include "tc_kernels.cuh"
+
+using namespace psvd;
+
+struct psvd_ctx {
+  psvd_config cfg;
+  cudaStream_t st = nullptr;
+  int num_sms = 0;
+  int64_t M = 0, ldu = 0;
+  int K = 0, maxB = 0, nmax = 0;
+  int kc = 0;  // current mode count
+  int64_t iteration = 0;
+  uint64_t sketch_counter = 0;
+  int cur = 0;
+  // FP32 modes (double-buffered) or BF16 hi/lo planes (tensor-core path)
+  float* U[2] = {nullptr, nullptr};
+  __nv_bfloat16* Uh[2] = {nullptr, nullptr};
+  __nv_bfloat16* Ul[2] = {nullptr, nullptr};
+  double* D[2] = {nullptr, nullptr};
+  double* partial = nullptr;
+  int64_t partial_cap = 0;  // doubles
+  double* G = nullptr;
+  SmallWork w{};
+  void* staging = nullptr;
+  size_t staging_bytes = 0;
+  float* Uf32_tmp = nullptr;  // FP32 view of hi/lo modes for get_modes / save
+  int host_info[4] = {0, 0, 0, 0};
+  int sticky_status = 0;
+};
+
+namespace {
+
+#define CK(x)                                     \
+  do {                                            \
+    cudaError_t err_ = (x);                       \
+    if (err_ != cudaSuccess) return PSVD_ERR_CUDA; \
+  } while (0)
+
+int elem_size(int dtype) {
+  switch (dtype) {
+    case PSVD_F32: return 4;
+    case PSVD_BF16: return 2;
+    case PSVD_F64: return 8;
+    default: return 0;
+  }
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+int dalloc(T** p, size_t count) {
+  if (count == 0) count = 1;
+  if (cudaMalloc((void**)p, sizeof(T) * count) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return PSVD_ERR_ALLOC;
+  }
+  return PSVD_OK;
+}
+
+// Device copy of a column-major input (staged if it lives in host memory).
+int stage_input(psvd_ctx* h, const void* A, int64_t lda, int64_t rows, int cols, int dtype,
+                const void** dev, int64_t* ld_dev) {
+  if (is_device_ptr(A)) {
+    *dev = A;
+    *ld_dev = lda;
+    return PSVD_OK;
+  }
+  const size_t es = (size_t)elem_size(dtype);
+  const size_t need = es * (size_t)rows * (size_t)cols;
+  if (need > h->staging_bytes) {
+    if (h->staging) {
+      CK(cudaStreamSynchronize(h->st));
+      cudaFree(h->staging);
+      h->staging = nullptr;
+    }
+    if (cudaMalloc(&h->staging, need) != cudaSuccess) {
+      cudaGetLastError();
+      h->staging_bytes = 0;
+      return PSVD_ERR_ALLOC;
+    }
+    h->staging_bytes = need;
+  }
+  CK(cudaMemcpy2DAsync(h->staging, es * rows, A, es * lda, es * rows, cols, cudaMemcpyHostToDevice,
+                       h->st));
+  *dev = h->staging;
+  *ld_dev = rows;
+  return PSVD_OK;
+}
+
+int ensure_partial(psvd_ctx* h, int64_t doubles) {
+  if (doubles <= h->partial_cap) return PSVD_OK;
+  if (h->partial) {
+    CK(cudaStreamSynchronize(h->st));
+    cudaFree(h->partial);
+    h->partial = nullptr;
+  }
+  if (dalloc(&h->partial, (size_t)doubles)) return PSVD_ERR_ALLOC;
+  h->partial_cap = doubles;
+  return PSVD_OK;
+}
+
+bool use_tc(const psvd_ctx* h) { return h->cfg.precision == PSVD_PREC_BF16_TC; }
+
+// Gram of the panel [U | A] (U = current modes, kc columns) -> H = S G S.
+// With G != nullptr the unscaled Gram is stored too.
+int panel_gram(psvd_ctx* h, const void* A, int64_t lda, int B, int dtype, int kc, double ff,
+               const double* D, double* G) {
+  const int n = kc + B;
+  if (use_tc(h)) {
+    int rc = tc_gram(h->Uh[h->cur], h->Ul[h->cur], h->ldu, kc, A, lda, B, dtype, h->M, h->num_sms,
+                     &h->partial, &h->partial_cap, h->st);
+    if (rc) return rc;
+    return tc_gram_reduce(h->partial, h->M, kc, B, h->num_sms, ff, D, G, h->w.H, h->st)
+               ? PSVD_ERR_CUDA
+               : PSVD_OK;
+  }
+  PanelF32 p{h->U[h->cur], h->ldu, kc, A, lda, dtype == PSVD_BF16 ? 1 : 0, h->M, n};
+  int nchunk;
+  int64_t rpc, pd;
+  gram_simt_plan(h->M, n, h->num_sms, &nchunk, &rpc, &pd);
+  if (int rc = ensure_partial(h, pd)) return rc;
+  CK(gram_simt_launch(p, nchunk, rpc, h->partial, h->st));
+  CK(gram_reduce_launch(h->partial, nchunk, n, kc, D, ff, G, h->w.H, h->w.info, h->st));
+  return PSVD_OK;
+}
+
+// One application of Algorithm 1's small solve + mode update; kc = 0 is the
+// initialisation I1-I2 (the panel is A0 alone).
+int step(psvd_ctx* h, const void* A, int64_t lda, int B, int dtype) {
+  const int kc = h->kc;
+  const int n = kc + B;
+  const int k1 = (h->K < n) ? h->K : n;
+  const double* Dcur = h->D[h->cur];
+  double* Dnext = h->D[h->cur ^ 1];
+  if (int rc = panel_gram(h, A, lda, B, dtype, kc, h->cfg.ff, Dcur, nullptr)) return rc;
+  SmallWork w = h->w;
+  w.Dnew = Dnext;
+  CK(small_solve_launch(w, n, kc, k1, Dcur, h->cfg.ff, /*refine_steps=*/2, /*max_sweeps=*/12,
+                        h->st));
+  if (use_tc(h)) {
+    int rc = tc_update(h->Uh[h->cur], h->Ul[h->cur], h->ldu, kc, A, lda, B, dtype, h->M, w.T3, n,
+                       k1, h->Uh[h->cur ^ 1], h->Ul[h->cur ^ 1], h->num_sms, h->st);
+    if (rc) return rc;
+  } else {
+    PanelF32 p{h->U[h->cur], h->ldu, kc, A, lda, dtype == PSVD_BF16 ? 1 : 0, h->M, n};
+    CK(update_simt_launch(p, w.T, k1, h->U[h->cur ^ 1], h->ldu, h->st));
+  }
+  h->cur ^= 1;
+  h->kc = k1;
+  h->iteration += 1;
+  return PSVD_OK;
+}
+
+int check_batch(psvd_ctx* h, const void* A, int64_t lda, int B, int dtype) {
+  if (!A || B < 1 || lda < h->M) return PSVD_ERR_INVALID_ARG;
+  if (dtype != PSVD_F32 && dtype != PSVD_BF16) return PSVD_ERR_INVALID_ARG;
+  if (use_tc(h) && dtype != PSVD_BF16) return PSVD_ERR_UNSUPPORTED;
+  if (B > h->maxB) return PSVD_ERR_SHAPE;
+  if (h->M < (int64_t)h->kc + B) return PSVD_ERR_SHAPE;
+  return PSVD_OK;
+}
+
+// Reads the device status word (synchronising) and folds it into a status code.
+int collect_status(psvd_ctx* h) {
+  CK(cudaMemcpyAsync(h->host_info, h->w.info, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  const int bits = h->host_info[2];
+  if (bits & 4) h->sticky_status = PSVD_ERR_NONFINITE;
+  if (h->sticky_status < 0) return h->sticky_status;
+  if (bits & 1) return PSVD_WARN_RANK_DEFICIENT;
+  if (bits & 2) return PSVD_WARN_NOT_CONVERGED;
+  return PSVD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* psvd_status_string(int s) {
+  switch (s) {
+    case PSVD_OK: return "ok";
+    case PSVD_WARN_RANK_DEFICIENT: return "warning: a kept singular value is numerically zero";
+    case PSVD_WARN_NOT_CONVERGED: return "warning: Jacobi eigen-solve reached its sweep limit";
+    case PSVD_ERR_INVALID_ARG: return "invalid argument";
+    case PSVD_ERR_NOT_INITIALIZED: return "handle not initialized (call psvd_initialize first)";
+    case PSVD_ERR_SHAPE: return "unsupported shape";
+    case PSVD_ERR_NONFINITE: return "non-finite value in the small factor";
+    case PSVD_ERR_CUDA: return "CUDA runtime error";
+    case PSVD_ERR_ALLOC: return "allocation failed";
+    case PSVD_ERR_IO: return "file I/O error or bad file";
+    case PSVD_ERR_UNSUPPORTED: return "unsupported for this precision or configuration";
+    default: return "unknown status";
+  }
+}
+
+int psvd_create(psvd_handle* out, const psvd_config* cfg) {
+  if (!out) return PSVD_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!cfg || cfg->M < 1 || cfg->K < 1 || cfg->max_batch < 1) return PSVD_ERR_INVALID_ARG;
+  if (!(cfg->ff > 0.0 && cfg->ff <= 1.0)) return PSVD_ERR_INVALID_ARG;
+  if (cfg->precision != PSVD_PREC_FP32 && cfg->precision != PSVD_PREC_BF16_TC)
+    return PSVD_ERR_INVALID_ARG;
+  if ((int64_t)cfg->K + cfg->max_batch > kMaxN) return PSVD_ERR_SHAPE;
+  if (cfg->low_rank) return PSVD_ERR_UNSUPPORTED;
+  psvd_ctx* h = new (std::nothrow) psvd_ctx();
+  if (!h) return PSVD_ERR_ALLOC;
+  h->cfg = *cfg;
+  h->st = (cudaStream_t)cfg->stream;
+  h->M = cfg->M;
+  h->ldu = ceil_div(cfg->M, 64) * 64;
+  h->K = cfg->K;
+  h->maxB = cfg->max_batch;
+  h->nmax = cfg->K + cfg->max_batch;
+  int dev = 0;
+  int rc = PSVD_OK;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return PSVD_ERR_CUDA;
+  }
+  const size_t nm = (size_t)h->nmax;
+  const size_t ucount = (size_t)h->ldu * (size_t)h->K;
+  for (int b = 0; b < 2 && !rc; ++b) {
+    if (use_tc(h)) {
+      rc = dalloc(&h->Uh[b], ucount);
+      if (!rc) rc = dalloc(&h->Ul[b], ucount);
+    } else {
+      rc = dalloc(&h->U[b], ucount);
+    }
+    if (!rc) rc = dalloc(&h->D[b], (size_t)h->K);
+  }
+  if (!rc) rc = dalloc(&h->G, nm * nm);
+  if (!rc) rc = dalloc(&h->w.H, nm * nm);
+  if (!rc) rc = dalloc(&h->w.X, nm * nm);
+  if (!rc) rc = dalloc(&h->w.lam, nm);
+  if (!rc) rc = dalloc(&h->w.W, nm * nm);
+  if (!rc) rc = dalloc(&h->w.S, nm * nm);
+  if (!rc) rc = dalloc(&h->w.R, nm * nm);
+  if (!rc) rc = dalloc(&h->w.E, nm * nm);
+  if (!rc) rc = dalloc(&h->w.Xn, nm * nm);
+  if (!rc) rc = dalloc(&h->w.lamJ, nm);
+  if (!rc) rc = dalloc(&h->w.T, nm * (size_t)h->K);
+  if (!rc) rc = dalloc(&h->w.T3, 3 * nm * (size_t)h->K);
+  if (!rc) rc = dalloc(&h->w.info, 4);
+  if (!rc && cudaMemsetAsync(h->w.info, 0, sizeof(int) * 4, h->st) != cudaSuccess) rc = PSVD_ERR_CUDA;
+  if (!rc) {
+    // zero the mode buffers once so that padded rows stay zero
+    for (int b = 0; b < 2 && !rc; ++b) {
+      if (use_tc(h)) {
+        if (cudaMemsetAsync(h->Uh[b], 0, ucount * 2, h->st) ||
+            cudaMemsetAsync(h->Ul[b], 0, ucount * 2, h->st))
+          rc = PSVD_ERR_CUDA;
+      } else if (cudaMemsetAsync(h->U[b], 0, ucount * 4, h->st)) {
+        rc = PSVD_ERR_CUDA;
+      }
+      if (!rc && cudaMemsetAsync(h->D[b], 0, sizeof(double) * h->K, h->st)) rc = PSVD_ERR_CUDA;
+    }
+  }
+  if (rc) {
+    psvd_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return PSVD_OK;
+}
+
+void psvd_destroy(psvd_handle h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->st);
+  for (int b = 0; b < 2; ++b) {
+    cudaFree(h->U[b]);
+    cudaFree(h->Uh[b]);
+    cudaFree(h->Ul[b]);
+    cudaFree(h->D[b]);
+  }
+  cudaFree(h->partial);
+  cudaFree(h->G);
+  cudaFree(h->w.H);
+  cudaFree(h->w.X);
+  cudaFree(h->w.lam);
+  cudaFree(h->w.W);
+  cudaFree(h->w.S);
+  cudaFree(h->w.R);
+  cudaFree(h->w.E);
+  cudaFree(h->w.Xn);
+  cudaFree(h->w.lamJ);
+  cudaFree(h->w.T);
+  cudaFree(h->w.T3);
+  cudaFree(h->w.info);
+  cudaFree(h->staging);
+  cudaFree(h->Uf32_tmp);
+  cudaGetLastError();
+  delete h;
+}
+
+int psvd_initialize(psvd_handle h, const void* A0, int64_t lda, int32_t B, int32_t dtype) {
+  if (!h) return PSVD_ERR_INVALID_ARG;
+  h->kc = 0;
+  if (int rc = check_batch(h, A0, lda, B, dtype)) return rc;
+  const void* Ad;
+  int64_t ldd;
+  if (int rc = stage_input(h, A0, lda, h->M, B, dtype, &Ad, &ldd)) return rc;
+  CK(cudaMemsetAsync(h->w.info, 0, sizeof(int) * 4, h->st));
+  h->sticky_status = 0;
+  h->iteration = 0;
+  return step(h, Ad, ldd, B, dtype);
+}
+
+int psvd_incorporate_data(psvd_handle h, const void* A, int64_t lda, int32_t B, int32_t dtype) {
+  if (!h) return PSVD_ERR_INVALID_ARG;
+  if (h->kc == 0) return PSVD_ERR_NOT_INITIALIZED;
+  if (int rc = check_batch(h, A, lda, B, dtype)) return rc;
+  const void* Ad;
+  int64_t ldd;
+  if (int rc = stage_input(h, A, lda, h->M, B, dtype, &Ad, &ldd)) return rc;
+  return step(h, Ad, ldd, B, dtype);
+}
+
+int psvd_num_modes(psvd_handle h) { return h ? h->kc : PSVD_ERR_INVALID_ARG; }
+
+int psvd_get_modes(psvd_handle h, float* U_out, int64_t ldo) {
+  if (!h || !U_out || ldo < h->M) return PSVD_ERR_INVALID_ARG;
+  if (h->kc == 0) return PSVD_ERR_NOT_INITIALIZED;
+  const float* src = h->U[h->cur];
+  if (use_tc(h)) {
+    if (!h->Uf32_tmp && dalloc(&h->Uf32_tmp, (size_t)h->ldu * h->K)) return PSVD_ERR_ALLOC;
+    CK(tc_modes_to_f32(h->Uh[h->cur], h->Ul[h->cur], h->ldu, h->M, h->kc, h->Uf32_tmp, h->st));
+    src = h->Uf32_tmp;
+  }
+  CK(cudaMemcpy2DAsync(U_out, sizeof(float) * ldo, src, sizeof(float) * h->ldu,
+                       sizeof(float) * h->M, h->kc, cudaMemcpyDefault, h->st));
+  return collect_status(h);
+}
+
+int psvd_get_singular_values(psvd_handle h, double* s_out) {
+  if (!h || !s_out) return PSVD_ERR_INVALID_ARG;
+  if (h->kc == 0) return PSVD_ERR_NOT_INITIALIZED;
+  CK(cudaMemcpyAsync(s_out, h->D[h->cur], sizeof(double) * h->kc, cudaMemcpyDefault, h->st));
+  return collect_status(h);
+}
+
+int psvd_last_info(psvd_handle h, int32_t* info4) {
+  if (!h || !info4) return PSVD_ERR_INVALID_ARG;
+  int rc = collect_status(h);
+  for (int i = 0; i < 4; ++i) info4[i] = h->host_info[i];
+  return rc;
+}
+
+int psvd_parallel_qr(psvd_handle h, const void* P, int64_t ldp, int32_t n, int32_t dtype,
+                     double* R_out) {
+  if (!h || !P || !R_out || n < 1 || ldp < h->M) return PSVD_ERR_INVALID_ARG;
+  if (dtype != PSVD_F32 && dtype != PSVD_BF16) return PSVD_ERR_INVALID_ARG;
+  if (n > h->nmax || h->M < n) return PSVD_ERR_SHAPE;
+  if (use_tc(h) && dtype != PSVD_BF16) return PSVD_ERR_UNSUPPORTED;
+  const void* Pd;
+  int64_t ldd;
+  if (int rc = stage_input(h, P, ldp, h->M, n, dtype, &Pd, &ldd)) return rc;
+  CK(cudaMemsetAsync(h->w.info, 0, sizeof(int) * 4, h->st));
+  if (int rc = panel_gram(h, Pd, ldd, n, dtype, 0, 1.0, h->D[h->cur], h->G)) return rc;
+  CK(cholesky_launch(h->G, n, h->w.X, h->w.info, h->st));
+  CK(cudaMemcpyAsync(R_out, h->w.X, sizeof(double) * n * n, cudaMemcpyDefault, h->st));
+  int rc = collect_status(h);
+  CK(cudaMemsetAsync(h->w.info, 0, sizeof(int) * 4, h->st));
+  h->sticky_status = 0;
+  return rc == PSVD_ERR_NONFINITE ? PSVD_ERR_NONFINITE : PSVD_OK;
+}
+
+int psvd_parallel_svd(psvd_handle h, const void* A, int64_t lda, const int64_t* part_offsets,
+                      int32_t nparts, int32_t N, int32_t dtype, int32_t r1, int32_t r2,
+                      float* U_out, int64_t ldu, double* L_out) {
+  (void)A; (void)lda; (void)part_offsets; (void)nparts; (void)N; (void)dtype; (void)r1; (void)r2;
+  (void)U_out; (void)ldu; (void)L_out;
+  if (!h) return PSVD_ERR_INVALID_ARG;
+  return PSVD_ERR_UNSUPPORTED;
+}
+
+int psvd_gaussian_sketch(uint64_t seed, uint64_t stream_id, int64_t rows, int64_t cols, float* out,
+                         void* stream) {
+  if (!out || rows < 0 || cols < 0) return PSVD_ERR_INVALID_ARG;
+  CK(gaussian_sketch_launch(seed, stream_id, rows, cols, out, (cudaStream_t)stream));
+  return PSVD_OK;
+}
+
+// File layout: magic "PSVD0001", psvd_config (stream zeroed), int64 iteration,
+// uint64 sketch counter, int32 kc, pad, kc doubles D, M*kc floats U (ld M).
+int psvd_save(psvd_handle h, const char* path) {
+  if (!h || !path) return PSVD_ERR_INVALID_ARG;
+  if (h->kc == 0) return PSVD_ERR_NOT_INITIALIZED;
+  const size_t nu = (size_t)h->M * h->kc;
+  float* U = (float*)malloc(sizeof(float) * (nu ? nu : 1));
+  double* D = (double*)malloc(sizeof(double) * h->kc);
+  if (!U || !D) { free(U); free(D); return PSVD_ERR_ALLOC; }
+  int rc = psvd_get_modes(h, U, h->M);
+  if (rc >= 0) rc = psvd_get_singular_values(h, D);
+  // TC handles keep the exact hi/lo pair: save it too so a reload is bit-identical
+  unsigned short* hl = nullptr;
+  if (rc >= 0 && use_tc(h)) {
+    hl = (unsigned short*)malloc(sizeof(unsigned short) * 2 * (nu ? nu : 1));
+    if (!hl) rc = PSVD_ERR_ALLOC;
+    if (rc >= 0 &&
+        (cudaMemcpy2D(hl, 2 * h->M, h->Uh[h->cur], 2 * h->ldu, 2 * h->M, h->kc, cudaMemcpyDeviceToHost) ||
+         cudaMemcpy2D(hl + nu, 2 * h->M, h->Ul[h->cur], 2 * h->ldu, 2 * h->M, h->kc, cudaMemcpyDeviceToHost)))
+      rc = PSVD_ERR_CUDA;
+  }
+  FILE* f = nullptr;
+  if (rc >= 0) f = fopen(path, "wb");
+  if (rc >= 0 && !f) rc = PSVD_ERR_IO;
+  if (rc >= 0) {
+    psvd_config c = h->cfg;
+    c.stream = nullptr;
+    const int32_t kc = h->kc, pad = 0;
+    bool ok = fwrite("PSVD0001", 1, 8, f) == 8 && fwrite(&c, sizeof c, 1, f) == 1 &&
+              fwrite(&h->iteration, 8, 1, f) == 1 && fwrite(&h->sketch_counter, 8, 1, f) == 1 &&
+              fwrite(&kc, 4, 1, f) == 1 && fwrite(&pad, 4, 1, f) == 1 &&
+              fwrite(D, sizeof(double), kc, f) == (size_t)kc && fwrite(U, sizeof(float), nu, f) == nu;
+    if (ok && hl) ok = fwrite(hl, 2, 2 * nu, f) == 2 * nu;
+    if (!ok) rc = PSVD_ERR_IO;
+  }
+  if (f) fclose(f);
+  free(U);
+  free(D);
+  free(hl);
+  return rc < 0 ? rc : PSVD_OK;
+}
+
+int psvd_load(psvd_handle* out, const char* path, void* stream) {
+  if (!out || !path) return PSVD_ERR_INVALID_ARG;
+  *out = nullptr;
+  FILE* f = fopen(path, "rb");
+  if (!f) return PSVD_ERR_IO;
+  char magic[8];
+  psvd_config c;
+  int64_t iteration;
+  uint64_t counter;
+  int32_t kc, pad;
+  int rc = PSVD_OK;
+  if (fread(magic, 1, 8, f) != 8 || memcmp(magic, "PSVD0001", 8) || fread(&c, sizeof c, 1, f) != 1 ||
+      fread(&iteration, 8, 1, f) != 1 || fread(&counter, 8, 1, f) != 1 || fread(&kc, 4, 1, f) != 1 ||
+      fread(&pad, 4, 1, f) != 1 || kc < 1 || kc > c.K || c.M < 1)
+    rc = PSVD_ERR_IO;
+  psvd_handle h = nullptr;
+  if (!rc) {
+    c.stream = stream;
+    rc = psvd_create(&h, &c);
+  }
+  const size_t nu = rc ? 0 : (size_t)c.M * kc;
+  float* U = rc ? nullptr : (float*)malloc(sizeof(float) * nu);
+  double* D = rc ? nullptr : (double*)malloc(sizeof(double) * kc);
+  unsigned short* hl = nullptr;
+  if (!rc && (!U || !D)) rc = PSVD_ERR_ALLOC;
+  if (!rc && (fread(D, sizeof(double), kc, f) != (size_t)kc || fread(U, sizeof(float), nu, f) != nu))
+    rc = PSVD_ERR_IO;
+  if (!rc && use_tc(h)) {
+    hl = (unsigned short*)malloc(2 * 2 * nu);
+    if (!hl || fread(hl, 2, 2 * nu, f) != 2 * nu) rc = PSVD_ERR_IO;
+  }
+  fclose(f);
+  if (!rc) {
+    if (use_tc(h)) {
+      if (cudaMemcpy2D(h->Uh[0], 2 * h->ldu, hl, 2 * c.M, 2 * c.M, kc, cudaMemcpyHostToDevice) ||
+          cudaMemcpy2D(h->Ul[0], 2 * h->ldu, hl + nu, 2 * c.M, 2 * c.M, kc, cudaMemcpyHostToDevice))
+        rc = PSVD_ERR_CUDA;
+    } else if (cudaMemcpy2D(h->U[0], 4 * h->ldu, U, 4 * c.M, 4 * c.M, kc, cudaMemcpyHostToDevice)) {
+      rc = PSVD_ERR_CUDA;
+    }
+    if (!rc && cudaMemcpy(h->D[0], D, sizeof(double) * kc, cudaMemcpyHostToDevice)) rc = PSVD_ERR_CUDA;
+  }
+  free(U);
+  free(D);
+  free(hl);
+  if (rc) {
+    psvd_destroy(h);
+    return rc;
+  }
+  h->cur = 0;
+  h->kc = kc;
+  h->iteration = iteration;
+  h->sketch_counter = counter;
+  *out = h;
+  return PSVD_OK;
+}
+
+}  // extern "C"

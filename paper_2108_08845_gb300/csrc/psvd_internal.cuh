@@ -1,0 +1,84 @@
+// Internal declarations shared by the library's translation units (not installed).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "psvd.h"
+
+namespace psvd {
+
+// Largest panel width n = K + B handled by the single-CTA eigen-solver (its packed
+// symmetric matrix plus eigenvector matrix, FP32, must fit in 227 KB of shared memory).
+constexpr int kMaxN = 192;
+// Extra eigenpairs refined beyond the kept K (covers the truncation boundary).
+constexpr int kRefineMargin = 8;
+
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+__device__ __forceinline__ float to_float(float x) { return x; }
+__device__ __forceinline__ float to_float(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+// ---------------------------------------------------------------- FP32 SIMT path
+// Panel [U | A]: U is M x kc FP32 (ldu), A is M x B (lda) of type TA.
+struct PanelF32 {
+  const float* U;
+  int64_t ldu;
+  int kc;
+  const void* A;
+  int64_t lda;
+  int a_bf16;  // 1: A is bfloat16, 0: float
+  int64_t M;
+  int n;  // kc + B
+};
+
+// Number of row chunks and partial-buffer doubles used by gram_simt for a panel.
+void gram_simt_plan(int64_t M, int n, int num_sms, int* nchunk, int64_t* rows_per_chunk,
+                    int64_t* partial_doubles);
+// Partial Grams of the panel over row chunks (FP64 per chunk, float-float inside).
+cudaError_t gram_simt_launch(const PanelF32& p, int nchunk, int64_t rows_per_chunk,
+                             double* partial, cudaStream_t st);
+// G = sum of partials (fixed order), H = S G S with S = diag(ff*D[0:kc], 1).
+// G may be null.  ldg = ldh = n.  A non-finite Gram entry sets info[2] bit 4.
+cudaError_t gram_reduce_launch(const double* partial, int nchunk, int n, int kc,
+                               const double* D, double ff, double* G, double* H, int* info,
+                               cudaStream_t st);
+// Unew (M x k1, ldo) = [U | A] * T (n x k1, FP32, ldt = n).
+cudaError_t update_simt_launch(const PanelF32& p, const float* T, int k1, float* Unew,
+                               int64_t ldo, cudaStream_t st);
+
+// ------------------------------------------------------------- small solve
+struct SmallWork {
+  double* H;      // n x n FP64 (scaled Gram), ld n
+  double* X;      // n x n FP64 eigenvector estimates (sorted), ld n
+  double* lam;    // n eigenvalue estimates (sorted, descending)
+  double* W;      // n x nJ scratch
+  double* S;      // n x nJ
+  double* R;      // n x nJ
+  double* E;      // n x nJ
+  double* Xn;     // n x nJ
+  double* lamJ;   // nJ refined eigenvalues
+  float* T;       // n x K FP32 update coefficients
+  __nv_bfloat16* T3;  // (3 n) x K BF16 triple split of T (tensor-core path)
+  double* Dnew;   // K new singular values
+  int* info;      // device int[4]: sweeps, refine steps, status, k1
+};
+
+// Eigen-decomposition of H (n x n) and the update coefficients:
+//   H = X diag(lam) X^T (descending), sigma = sqrt(lam[0:k1]),
+//   T = S X[:, 0:k1] diag(1/sigma), Dnew = sigma.
+cudaError_t small_solve_launch(const SmallWork& w, int n, int kc, int k1, const double* D,
+                               double ff, int refine_steps, int max_sweeps, cudaStream_t st);
+// FP64 Cholesky R^T R = G (n x n) into R (ld n, upper); info[2] = status.
+cudaError_t cholesky_launch(const double* G, int n, double* R, int* info, cudaStream_t st);
+
+// -------------------------------------------------------------------- Philox
+cudaError_t gaussian_sketch_launch(uint64_t seed, uint64_t stream_id, int64_t rows, int64_t cols,
+                                   float* out, cudaStream_t st);
+
+// ---------------------------------------------------------------- misc kernels
+cudaError_t copy_modes_f32_launch(const float* U, int64_t ldu, int64_t M, int k, float* out,
+                                  int64_t ldo, cudaStream_t st);
+
+}  // namespace psvd

@@ -1,0 +1,396 @@
+// Small (K+B) x (K+B) solve of the per-batch update (Algorithm 1 steps 2, 3, 5).
+//
+// The paper takes the SVD of the panel's R factor.  Here the panel is represented
+// by H = R^T R = S G S (its scaled Gram), and its singular triplets follow from
+// the eigen-decomposition H = V diag(lambda) V^T: sigma = sqrt(lambda),
+// right singular vectors V, and Q U~ = P V diag(1/sigma) (step 4).
+//
+// The eigen-solve is built for a GPU whose FP64 rate is ~2 FMA/clk/SM (FP32
+// ~114): O(n^3) FP64 work only appears as small GEMMs spread over all SMs.
+//   1. jacobi_eig_kernel on H: cyclic two-sided Jacobi in FP32 on one CTA (packed
+//      symmetric matrix and eigenvector matrix in shared memory, round-robin
+//      parallel ordering: n/2 disjoint rotations per round).  Eigenvalues that
+//      arise by cancellation between columns are only resolved to ~u32 ||H||.
+//   2. H2 = X1^T H X1 in FP64 (GEMMs).  H2 is graded: the resolved part is
+//      nearly diagonal and the unresolved part is a block of size ~u32 ||H||.
+//   3. jacobi_eig_kernel on H2 in FP32; on a graded matrix two-sided Jacobi is
+//      relatively accurate (Demmel & Veselic, 1992), so the combined basis
+//      X = X1 X2 is accurate to ~u32^2 ||H|| in absolute terms.
+//   4. Ogita & Aishima (2018) iterative refinement (RefSyEv) of the leading
+//      eigenpairs in FP64 (GEMMs), quadratically convergent from X.
+// finalize_kernel sorts, truncates to k1 and forms T = S V_k1 diag(1/sigma).
+#include <math.h>
+
+#include "psvd_internal.cuh"
+
+namespace psvd {
+namespace {
+
+constexpr int JT = 1024;
+// Resolution of a Gram-based factorisation: eigenvalues of the scaled Gram below
+// kLambdaFloor * lambda_max (singular values below sqrt of that times sigma_max)
+// are at the rounding level of the Gram and are not resolved; such kept modes
+// are set to zero and reported as PSVD_WARN_RANK_DEFICIENT.
+constexpr double kLambdaFloor = 1e-9;
+constexpr double kSigmaFloor = 3.1622776601683795e-5;  // sqrt(kLambdaFloor)
+
+__device__ __forceinline__ int pidx(int i, int j) {  // packed upper, i <= j
+  return j * (j + 1) / 2 + i;
+}
+__device__ __forceinline__ int pidx_any(int a, int b) { return a <= b ? pidx(a, b) : pidx(b, a); }
+
+// Round-robin ("circle") tournament on N (even) players: in round r player N-1
+// sits at position 0 and player (k - 1 + r) mod (N - 1) at position k >= 1;
+// pair i meets positions i and N-1-i.  Every pair meets once per N-1 rounds.
+__device__ __forceinline__ int tour_player(int pos, int r, int N) {
+  return pos == 0 ? N - 1 : (pos - 1 + r) % (N - 1);
+}
+
+__global__ void __launch_bounds__(JT) jacobi_eig_kernel(const double* __restrict__ H, int n,
+                                                        double* __restrict__ X,
+                                                        double* __restrict__ lam, int max_sweeps,
+                                                        float tol, int* __restrict__ info,
+                                                        int info_slot, int flag_unconverged) {
+  extern __shared__ __align__(16) float sm[];
+  __shared__ float cs_c[kMaxN / 2], cs_s[kMaxN / 2];
+  __shared__ int pp[kMaxN / 2], qq[kMaxN / 2];
+  __shared__ int rot_any;
+  __shared__ int rank_of[kMaxN];
+  const int N = (n + 1) & ~1;
+  const int P = N / 2;
+  const int tid = threadIdx.x;
+  const int npk = ((N * (N + 1) / 2) + 3) & ~3;
+  float* Hp = sm;        // packed upper triangle of the working matrix
+  float* V = sm + npk;   // N x N eigenvector matrix, column-major
+
+  for (int e = tid; e < N * N; e += JT) {
+    const int i = e % N, j = e / N;
+    if (i <= j) Hp[pidx(i, j)] = (i < n && j < n) ? (float)H[i + (int64_t)j * n] : 0.f;
+    V[e] = (i == j) ? 1.f : 0.f;
+  }
+  __syncthreads();
+
+  int sweep = 0;
+  bool converged = false;
+  while (sweep < max_sweeps) {
+    ++sweep;
+    if (tid == 0) rot_any = 0;
+    __syncthreads();
+    for (int r = 0; r < N - 1; ++r) {
+      // rotation of each disjoint pair (p, q): zeroes H_pq (Golub & Van Loan sym.schur2)
+      if (tid < P) {
+        int p = tour_player(tid, r, N), q = tour_player(N - 1 - tid, r, N);
+        if (p > q) { const int t = p; p = q; q = t; }
+        const float app = Hp[pidx(p, p)], aqq = Hp[pidx(q, q)], apq = Hp[pidx(p, q)];
+        float c = 1.f, s = 0.f;
+        if (apq != 0.f && fabsf(apq) > tol * sqrtf(fabsf(app)) * sqrtf(fabsf(aqq))) {
+          const float th = (aqq - app) / (2.f * apq);
+          const float at = fabsf(th);
+          float t = (at > 1e18f) ? 0.5f / at : 1.f / (at + sqrtf(1.f + th * th));
+          t = (th >= 0.f) ? t : -t;
+          c = rsqrtf(1.f + t * t);
+          s = t * c;
+          Hp[pidx(p, p)] = app - t * apq;
+          Hp[pidx(q, q)] = aqq + t * apq;
+          Hp[pidx(p, q)] = 0.f;
+          rot_any = 1;
+        }
+        pp[tid] = p;
+        qq[tid] = q;
+        cs_c[tid] = c;
+        cs_s[tid] = s;
+      }
+      __syncthreads();
+      // off-diagonal 2x2 blocks: B_kl <- J_k^T B_kl J_l (each entry in one block)
+      for (int e = tid; e < P * P; e += JT) {
+        const int k = e / P, l = e % P;
+        if (k >= l) continue;
+        const float sk = cs_s[k], sl = cs_s[l];
+        if (sk == 0.f && sl == 0.f) continue;
+        const float ck = cs_c[k], cl = cs_c[l];
+        const int pk = pp[k], qk = qq[k], pl = pp[l], ql = qq[l];
+        const int i11 = pidx_any(pk, pl), i12 = pidx_any(pk, ql), i21 = pidx_any(qk, pl),
+                  i22 = pidx_any(qk, ql);
+        const float x11 = Hp[i11], x12 = Hp[i12], x21 = Hp[i21], x22 = Hp[i22];
+        const float y11 = ck * x11 - sk * x21, y12 = ck * x12 - sk * x22;
+        const float y21 = sk * x11 + ck * x21, y22 = sk * x12 + ck * x22;
+        Hp[i11] = cl * y11 - sl * y12;
+        Hp[i12] = sl * y11 + cl * y12;
+        Hp[i21] = cl * y21 - sl * y22;
+        Hp[i22] = sl * y21 + cl * y22;
+      }
+      // eigenvector columns: V <- V J
+      for (int e = tid; e < P * N; e += JT) {
+        const int k = e / N, i = e % N;
+        const float s = cs_s[k];
+        if (s == 0.f) continue;
+        const float c = cs_c[k];
+        float* vp = &V[i + pp[k] * N];
+        float* vq = &V[i + qq[k] * N];
+        const float a = *vp, b = *vq;
+        *vp = c * a - s * b;
+        *vq = s * a + c * b;
+      }
+      __syncthreads();
+    }
+    if (!rot_any) {
+      converged = true;
+      break;
+    }
+  }
+  // sort eigenvalues descending (stable on index) and write FP64 outputs
+  if (tid < n) {
+    const float li = Hp[pidx(tid, tid)];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const float lj = Hp[pidx(j, j)];
+      rank += (lj > li) || (lj == li && j < tid);
+    }
+    rank_of[tid] = rank;
+    lam[rank] = (double)li;
+  }
+  __syncthreads();
+  for (int e = tid; e < n * n; e += JT) {
+    const int i = e % n, j = e / n;
+    X[i + (int64_t)rank_of[j] * n] = (double)V[i + j * N];
+  }
+  if (tid == 0) {
+    info[info_slot] = sweep;
+    if (!converged && flag_unconverged) atomicOr(&info[2], 2);
+  }
+}
+
+// C (m x nn) = alpha * op(A) * B + beta * Cin, FP64, column-major.
+// op(A) = A (lda >= m) or A^T (A is k x m).  8 x 8 outputs per CTA.
+template <bool TRANS_A>
+__global__ void __launch_bounds__(64) dgemm_kernel(int m, int nn, int k, double alpha,
+                                                   const double* __restrict__ A, int lda,
+                                                   const double* __restrict__ B, int ldb,
+                                                   double beta, const double* __restrict__ Cin,
+                                                   int ldci, double* __restrict__ C, int ldc) {
+  __shared__ double As[8][33];
+  __shared__ double Bs[32][9];
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+  const int row = blockIdx.x * 8 + tx, col = blockIdx.y * 8 + ty;
+  double acc = 0.0;
+  for (int k0 = 0; k0 < k; k0 += 32) {
+    for (int e = threadIdx.x; e < 8 * 32; e += 64) {
+      const int r = e % 8, kk = e / 8;  // A tile: rows blockIdx.x*8 + r, k index k0 + kk
+      const int gr = blockIdx.x * 8 + r, gk = k0 + kk;
+      double v = 0.0;
+      if (gr < m && gk < k) v = TRANS_A ? A[gk + (int64_t)gr * lda] : A[gr + (int64_t)gk * lda];
+      As[r][kk] = v;
+      const int c = e / 32, kb = e % 32;  // B tile: k index k0 + kb, column blockIdx.y*8 + c
+      const int gc = blockIdx.y * 8 + c, gkb = k0 + kb;
+      Bs[kb][c] = (gc < nn && gkb < k) ? B[gkb + (int64_t)gc * ldb] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) acc = fma(As[tx][kk], Bs[kk][ty], acc);
+    __syncthreads();
+  }
+  if (row < m && col < nn) {
+    double v = alpha * acc;
+    if (beta != 0.0) v = fma(beta, Cin[row + (int64_t)col * ldci], v);
+    C[row + (int64_t)col * ldc] = v;
+  }
+}
+
+// One Ogita-Aishima correction for column j of the refined set J = [0, nJ):
+//   RR = I - X^T X (column j),  lt_j = S_jj / (X^T X)_jj,
+//   E_ij = (S_ij + lt_j RR_ij) / (lt_j - lt_i)   for well-separated i,
+//   E_ij = RR_ij / 2                             within a cluster (and i = j),
+// with eigenvalue estimates lt_i = S_ii/(X^T X)_ii for i < nJ and the FP32
+// Jacobi values beyond.  The cluster test is relative, |lt_j - lt_i| <=
+// tau * max(|lt_i|, |lt_j|), since the Jacobi stage is relatively accurate on
+// graded matrices (OA's absolute threshold would merge every small eigenvalue).
+// Eigenpairs below the Gram's resolution (lambda <= kLambdaFloor * lambda_max)
+// carry no information and are left unrefined (E column zero).
+__global__ void oa_correct_kernel(int n, int nJ, const double* __restrict__ S,
+                                  const double* __restrict__ XtX, const double* __restrict__ lam,
+                                  double tau, double* __restrict__ E, double* __restrict__ lamJ,
+                                  int* __restrict__ info) {
+  const int j = blockIdx.x;
+  const double* Sj = S + (int64_t)j * n;
+  const double* Rj = XtX + (int64_t)j * n;
+  const double ltj = Sj[j] / Rj[j];
+  if (!(lam[j] > kLambdaFloor * lam[0])) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) E[i + (int64_t)j * n] = 0.0;
+    if (threadIdx.x == 0) lamJ[j] = lam[j];
+    return;
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double rr = ((i == j) ? 1.0 : 0.0) - Rj[i];
+    double e;
+    if (i == j) {
+      e = 0.5 * rr;
+    } else {
+      const double lti = (i < nJ) ? S[i + (int64_t)i * n] / XtX[i + (int64_t)i * n] : lam[i];
+      const double gap = ltj - lti;
+      if (fabs(gap) > tau * fmax(fabs(ltj), fabs(lti)))
+        e = (Sj[i] + ltj * rr) / gap;
+      else
+        e = 0.5 * rr;
+    }
+    E[i + (int64_t)j * n] = e;
+  }
+  if (threadIdx.x == 0) {
+    lamJ[j] = ltj;
+    if (!isfinite(ltj)) atomicOr(&info[2], 4);
+  }
+}
+
+__global__ void copy_cols_kernel(const double* __restrict__ src, double* __restrict__ dst,
+                                 int64_t count) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < count) dst[e] = src[e];
+}
+
+// Sort the refined eigenpairs, truncate to k1 and form the update coefficients.
+__global__ void finalize_kernel(int n, int nJ, int kc, int k1, const double* __restrict__ X,
+                                const double* __restrict__ lamJ, const double* __restrict__ D,
+                                double ff, float* __restrict__ T, __nv_bfloat16* __restrict__ T3,
+                                double* __restrict__ Dnew, int* __restrict__ info) {
+  __shared__ int order[kMaxN];
+  __shared__ double sig[kMaxN];
+  const int tid = threadIdx.x;
+  if (tid < nJ) {
+    const double li = lamJ[tid];
+    int rank = 0;
+    for (int j = 0; j < nJ; ++j) {
+      const double lj = lamJ[j];
+      rank += (lj > li) || (lj == li && j < tid);
+    }
+    order[rank] = tid;
+  }
+  __syncthreads();
+  if (tid < k1) {
+    const double l = lamJ[order[tid]];
+    sig[tid] = (l > 0.0) ? sqrt(l) : 0.0;
+    if (!isfinite(l)) atomicOr(&info[2], 4);
+  }
+  __syncthreads();
+  const double s0 = sig[0];
+  if (tid < k1) {
+    double s = sig[tid];
+    if (!(s > kSigmaFloor * s0) || !isfinite(s)) {
+      if (!isfinite(s) || !isfinite(s0)) atomicOr(&info[2], 4);
+      else atomicOr(&info[2], 1);
+      s = 0.0;
+      sig[tid] = 0.0;
+    }
+    Dnew[tid] = s;
+  }
+  __syncthreads();
+  for (int e = tid; e < n * k1; e += blockDim.x) {
+    const int i = e % n, k = e / n;
+    const double s = sig[k];
+    const double scale = (i < kc) ? ff * D[i] : 1.0;
+    const double t = (s > 0.0) ? scale * X[i + (int64_t)order[k] * n] / s : 0.0;
+    T[i + (int64_t)k * n] = (float)t;
+    if (T3) {
+      // exact triple split t = h + m + l (24 significant bits) for BF16 operands
+      const __nv_bfloat16 h = __float2bfloat16_rn((float)t);
+      const double r1 = t - (double)__bfloat162float(h);
+      const __nv_bfloat16 md = __float2bfloat16_rn((float)r1);
+      const double r2 = r1 - (double)__bfloat162float(md);
+      const __nv_bfloat16 lo = __float2bfloat16_rn((float)r2);
+      T3[i + (int64_t)k * 3 * n] = h;
+      T3[n + i + (int64_t)k * 3 * n] = md;
+      T3[2 * n + i + (int64_t)k * 3 * n] = lo;
+    }
+  }
+  if (tid == 0) info[3] = k1;
+}
+
+// Upper Cholesky R^T R = G (FP64, one CTA): row i of R from rows < i.
+__global__ void cholesky_kernel(const double* __restrict__ G, int n, double* __restrict__ R,
+                                int* __restrict__ info) {
+  __shared__ double piv;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) R[e] = 0.0;
+  __syncthreads();
+  for (int i = 0; i < n; ++i) {
+    if (threadIdx.x == 0) {
+      double s = G[i + (int64_t)i * n];
+      for (int k = 0; k < i; ++k) s -= R[k + (int64_t)i * n] * R[k + (int64_t)i * n];
+      if (!(s > 0.0) || !isfinite(s)) {
+        atomicOr(&info[2], 4);
+        s = 0.0;
+      }
+      piv = sqrt(s);
+      R[i + (int64_t)i * n] = piv;
+    }
+    __syncthreads();
+    const double d = piv;
+    for (int j = i + 1 + threadIdx.x; j < n; j += blockDim.x) {
+      double s = G[i + (int64_t)j * n];
+      for (int k = 0; k < i; ++k) s -= R[k + (int64_t)i * n] * R[k + (int64_t)j * n];
+      R[i + (int64_t)j * n] = (d > 0.0) ? s / d : 0.0;
+    }
+    __syncthreads();
+  }
+}
+
+template <bool TA>
+cudaError_t dgemm(int m, int nn, int k, double alpha, const double* A, int lda, const double* B,
+                  int ldb, double beta, const double* Cin, int ldci, double* C, int ldc,
+                  cudaStream_t st) {
+  dim3 grid((unsigned)ceil_div(m, 8), (unsigned)ceil_div(nn, 8));
+  dgemm_kernel<TA><<<grid, 64, 0, st>>>(m, nn, k, alpha, A, lda, B, ldb, beta, Cin, ldci, C, ldc);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t jacobi_smem_bytes(int n) {
+  const int N = (n + 1) & ~1;
+  const int npk = ((N * (N + 1) / 2) + 3) & ~3;
+  return sizeof(float) * ((size_t)npk + (size_t)N * N);
+}
+
+cudaError_t small_solve_launch(const SmallWork& w, int n, int kc, int k1, const double* D,
+                               double ff, int refine_steps, int max_sweeps, cudaStream_t st) {
+  const size_t smem = jacobi_smem_bytes(n);
+  cudaError_t e = cudaFuncSetAttribute(jacobi_eig_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  // stage 1: FP32 Jacobi on H -> X1 (in E), eigenvalues (in lamJ, unused)
+  const int stage1_sweeps = (max_sweeps < 8) ? max_sweeps : 8;
+  jacobi_eig_kernel<<<1, JT, smem, st>>>(w.H, n, w.E, w.lamJ, stage1_sweeps, 2e-6f, w.info, 0, 0);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // stage 2: H2 = X1^T H X1 (FP64, in S), FP32 Jacobi on H2 -> X2 (in R), lam
+  if ((e = dgemm<false>(n, n, n, 1.0, w.H, n, w.E, n, 0.0, nullptr, n, w.W, n, st))) return e;
+  if ((e = dgemm<true>(n, n, n, 1.0, w.E, n, w.W, n, 0.0, nullptr, n, w.S, n, st))) return e;
+  jacobi_eig_kernel<<<1, JT, smem, st>>>(w.S, n, w.R, w.lam, max_sweeps, 2e-6f, w.info, 1, 1);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // X = X1 X2
+  if ((e = dgemm<false>(n, n, n, 1.0, w.E, n, w.R, n, 0.0, nullptr, n, w.X, n, st))) return e;
+  const int nJ = (k1 + kRefineMargin < n) ? k1 + kRefineMargin : n;
+  for (int it = 0; it < refine_steps; ++it) {
+    // W = H X_J ; S = X^T W ; XtX = X^T X_J
+    if ((e = dgemm<false>(n, nJ, n, 1.0, w.H, n, w.X, n, 0.0, nullptr, n, w.W, n, st))) return e;
+    if ((e = dgemm<true>(n, nJ, n, 1.0, w.X, n, w.W, n, 0.0, nullptr, n, w.S, n, st))) return e;
+    if ((e = dgemm<true>(n, nJ, n, 1.0, w.X, n, w.X, n, 0.0, nullptr, n, w.R, n, st))) return e;
+    oa_correct_kernel<<<nJ, 256, 0, st>>>(n, nJ, w.S, w.R, w.lam, 1e-5, w.E, w.lamJ, w.info);
+    if ((e = cudaGetLastError())) return e;
+    // X_J <- X_J + X E
+    if ((e = dgemm<false>(n, nJ, n, 1.0, w.X, n, w.E, n, 1.0, w.X, n, w.Xn, n, st))) return e;
+    const int64_t cnt = (int64_t)n * nJ;
+    copy_cols_kernel<<<(unsigned)ceil_div(cnt, 256), 256, 0, st>>>(w.Xn, w.X, cnt);
+    if ((e = cudaGetLastError())) return e;
+  }
+  if (refine_steps == 0) {
+    const int64_t cnt = nJ;
+    copy_cols_kernel<<<(unsigned)ceil_div(cnt, 256), 256, 0, st>>>(w.lam, w.lamJ, cnt);
+    if ((e = cudaGetLastError())) return e;
+  }
+  finalize_kernel<<<1, 256, 0, st>>>(n, nJ, kc, k1, w.X, w.lamJ, D, ff, w.T, w.T3, w.Dnew, w.info);
+  return cudaGetLastError();
+}
+
+cudaError_t cholesky_launch(const double* G, int n, double* R, int* info, cudaStream_t st) {
+  cholesky_kernel<<<1, 256, 0, st>>>(G, n, R, info);
+  return cudaGetLastError();
+}
+
+}  // namespace psvd

@@ -1,0 +1,38 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports every
+entry point that include/psvd.h declares (no compute calls: CPU only)."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+from paper_2108_08845_gb300 import build, psvd
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(psvd_\w+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.mark.skipif(shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"),
+                    reason="nvcc not available")
+def test_library_exports_every_declared_symbol():
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    names = _declared()
+    assert "psvd_incorporate_data" in names and len(names) >= 14
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, f"missing exports: {missing}"
+
+
+def test_status_strings_without_gpu():
+    assert psvd.status_string(psvd.PSVD_ERR_SHAPE) == "unsupported shape"
+    assert psvd.status_string(12345) == "unknown status"
