@@ -1,0 +1,349 @@
+"""Benchmark: streaming-SVD updates per second (Algorithm 1, Sec. 3.1) on GB300.
+
+Workload (default): M = 2^23 grid points (a 2048 x 4096 grid flattened), K = 64
+modes, batches of B = 128 snapshots stored in BF16, forget factor 0.95;
+snapshots are sums of 256 travelling-wave modes (periodic Gaussian random fields
+with correlation length 16 cells, sin(w_j t + phi_j), amplitudes j^-1.2) plus
+N(0, 1e-4^2) noise, generated on the GPU.  Each batch is 2 GiB, larger than the
+129 MB L2, so no flush is needed between timed steps.
+
+A step is one psvd_incorporate_data call: panel Gram, small eigen-solve and
+mode update.  W untimed warm-up steps follow psvd_initialize, then exactly K
+steps are timed with CUDA events on the library's stream, bracketed by a
+barrier and torch.cuda.synchronize().  Under torchrun every rank runs an
+independent replica on its own GPU (the path has no exchange step on one GPU);
+value = all ranks' snapshots / the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle (the only reference implementation:
+the paper has no code of its own to install) on a bounded sample of the same
+workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "snapshots/s at M=2^23,K=64: FP32 plain vs BF16-TC+refine, σ rel err ≤1e-4"
+UNIT = "snapshots/s"
+
+NY, NX, NMODES, DECAY, NOISE, CORR = 2048, 4096, 256, 1.2, 1e-4, 16.0
+M_FULL = NY * NX
+K_MODES, BATCH, FF, SEED = 64, 128, 0.95, 1236
+WORKLOAD = ("M=2^23 (2048x4096 grid), K=64, B=128 BF16 snapshots, ff=0.95, "
+            "travelling waves: 256 modes, amplitudes j^-1.2, noise 1e-4")
+
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 FMA units x 2 flops x max SM clock
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples taken while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def make_batches(device, count: int):
+    import torch
+
+    from paper_2108_08845_gb300 import synthetic
+    gen = synthetic.TravellingWaves(NY, NX, NMODES, DECAY, NOISE, SEED, corr_len=CORR,
+                                    device=device, dtype=torch.float32)
+    out = []
+    for i in range(count):
+        out.append(gen.batch(i, BATCH).to(torch.bfloat16).T.contiguous().T)
+    del gen
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_arm(psvd, batches, precision, steps, warmup, stream, sampler=None):
+    """Times `steps` updates after initialise + warm-up; returns a result dict."""
+    import torch
+
+    h = psvd.psvd_create(M_FULL, K_MODES, BATCH, FF, precision, stream=stream)
+    try:
+        nb = len(batches)
+        psvd.psvd_initialize(h, batches[0])
+        for i in range(warmup):
+            psvd.psvd_incorporate_data(h, batches[1 + i % (nb - 1)])
+        psvd.psvd_set_profiling(h, True)
+        torch.cuda.synchronize()
+        if torch.distributed.is_initialized():
+            torch.distributed.barrier()
+        if sampler:
+            sampler.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(steps):
+            psvd.psvd_incorporate_data(h, batches[1 + (warmup + i) % (nb - 1)])
+        e1.record(stream)
+        e1.synchronize()
+        torch.cuda.synchronize()
+        clocks = sampler.stop() if sampler else None
+        ms = e0.elapsed_time(e1)
+        prof_ms, prof_cnt, launches = psvd.psvd_get_profile(h)
+        s = torch.empty(K_MODES, dtype=torch.float64, device="cuda")
+        status = psvd.psvd_get_singular_values(h, s)
+        _, info = psvd.psvd_last_info(h)
+    finally:
+        psvd.psvd_destroy(h)
+    return {"ms": ms, "prof_ms": prof_ms, "prof_cnt": prof_cnt, "launches": launches,
+            "clocks": clocks, "sigma": s.cpu().tolist(), "status": status, "info": info}
+
+
+def run_e2e(psvd, batches, precision, steps, stream):
+    """Same metric through the public API with pinned host inputs and a D2H read."""
+    import torch
+
+    nh = min(4, len(batches) - 1)
+    host = []
+    for b in batches[1:1 + nh]:  # column-major pinned host copies
+        hb = torch.empty((b.shape[1], b.shape[0]), dtype=b.dtype, pin_memory=True).T
+        hb.copy_(b)
+        host.append(hb)
+    s_host = torch.empty(K_MODES, dtype=torch.float64).pin_memory()
+    h = psvd.psvd_create(M_FULL, K_MODES, BATCH, FF, precision, stream=stream)
+    try:
+        psvd.psvd_initialize(h, batches[0])
+        psvd.psvd_incorporate_data(h, host[0])  # warm the staging buffer
+        psvd.psvd_get_singular_values(h, s_host)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(steps):
+            psvd.psvd_incorporate_data(h, host[i % nh])
+            psvd.psvd_get_singular_values(h, s_host)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    finally:
+        psvd.psvd_destroy(h)
+    return {"value": steps * BATCH / dt, "unit": UNIT,
+            "h2d_bytes_per_step": M_FULL * BATCH * 2, "d2h_bytes_per_step": K_MODES * 8,
+            "steps": steps}
+
+
+def roofline(res, precision, hbm_peak, peak_kind):
+    """Roofline entry for the phase with the largest device time."""
+    phases = ["gram", "small_solve", "update"]
+    avg = [res["prof_ms"][i] / max(1, res["prof_cnt"][i]) for i in range(3)]
+    dom = max(range(3), key=lambda i: res["prof_ms"][i])
+    n = K_MODES + BATCH
+    if precision == "bf16_tc":
+        byt = {0: M_FULL * (4 * K_MODES + 2 * BATCH),
+               2: M_FULL * (4 * K_MODES + 2 * BATCH + 4 * K_MODES)}
+        pick = dom if dom in byt else 2
+        achieved = byt[pick] / (avg[pick] * 1e-3) / 1e9
+        return {"bound": "hbm", "kernel": phases[pick], "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                "peak_source": peak_kind, "avg_ms": avg[pick]}, avg
+    flops = {0: M_FULL * n * (n + 1), 2: 2 * M_FULL * n * K_MODES}
+    pick = dom if dom in flops else 0
+    achieved = flops[pick] / (avg[pick] * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": phases[pick], "achieved": achieved,
+            "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+            "traffic": None, "peak_source": "FP32 units x max clock", "avg_ms": avg[pick]}, avg
+
+
+def cpu_sample(updates: int = 2, ny: int = 128, nx: int = 256):
+    """Oracle on a bounded sample: a ny x nx grid of the same recipe, K = 64, B = 128,
+    initialise + `updates` updates; per-update time scaled by M_full / M_sample
+    (the oracle's work per update is linear in M)."""
+    import torch
+
+    import oracle
+    from paper_2108_08845_gb300 import synthetic
+    gen = synthetic.TravellingWaves(ny, nx, NMODES, DECAY, NOISE, SEED, corr_len=CORR)
+    bs = [gen.batch(i, BATCH).to(torch.bfloat16).double().numpy() for i in range(updates + 1)]
+    U, D = oracle.stream_initialize(bs[0], K_MODES)
+    t0 = time.perf_counter()
+    for b in bs[1:]:
+        U, D = oracle.stream_update(U, D, b, FF, K_MODES)
+    dt = (time.perf_counter() - t0) / updates
+    m = ny * nx
+    scaled = dt * (M_FULL / m)
+    return {"value": BATCH / scaled, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{updates} updates at M={m} ({ny}x{nx} grid), K=64, B=128, "
+                      f"{dt:.2f} s per update, scaled by M_full/M_sample={M_FULL // m}"}
+
+
+def reference_main(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    samples = []
+    for _ in range(args.warmup):
+        cpu_sample(1, 64, 128)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        samples.append(cpu_sample(1, 64, 128))
+    wall = time.perf_counter() - t0
+    v = statistics.median(s["value"] for s in samples)
+    cb = dict(samples[0])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": BATCH / v * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "M": M_FULL, "K": K_MODES,
+                                            "B": BATCH, "ff": FF},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=24)
+    ap.add_argument("--warmup", type=int, default=4)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="both", choices=["both", "fp32", "bf16_tc"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=8)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return reference_main(args)
+
+    import torch
+
+    from paper_2108_08845_gb300 import psvd
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.current_stream()
+    hbm_peak, bf16_peak, peak_kind = _peaks()
+
+    arms = {"both": ["bf16_tc", "fp32"], "fp32": ["fp32"], "bf16_tc": ["bf16_tc"]}[args.precision]
+    prec_code = {"fp32": psvd.PSVD_PREC_FP32, "bf16_tc": psvd.PSVD_PREC_BF16_TC}
+    nb = min(32, 1 + args.warmup + args.steps)
+    batches = make_batches("cuda", nb)
+    results = {}
+    for arm in arms:
+        sampler = ClockSampler(local) if rank == 0 else None
+        try:
+            results[arm] = run_arm(psvd, batches, prec_code[arm], args.steps, args.warmup, stream,
+                                   sampler)
+        except psvd.PsvdError as e:
+            if e.status != psvd.PSVD_ERR_UNSUPPORTED or args.precision != "both":
+                raise
+            results[arm] = None  # the tensor-core path is not available in this build
+    head = next(a for a in arms if results.get(a))
+    r = results[head]
+    ms_local = r["ms"]
+    if ws > 1:
+        t = torch.tensor([ms_local], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_max = float(t.item())
+    else:
+        ms_max = ms_local
+    value = ws * args.steps * BATCH / (ms_max * 1e-3)
+    e2e = run_e2e(psvd, batches, prec_code[head], args.e2e_steps, stream)
+    if ws > 1:
+        t = torch.tensor([e2e["value"]], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MIN)
+        e2e["value"] = float(t.item()) * ws
+    if rank == 0:
+        rf, avg = roofline(r, head, hbm_peak, peak_kind)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "bf16" if head == "bf16_tc" else "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "M": M_FULL, "K": K_MODES, "B": BATCH, "ff": FF,
+                           "precision": head, "replicas": ws,
+                           "l2": "inputs larger than L2 (2 GiB per batch), no flush"},
+                "roofline": rf, "clocks": r["clocks"], "e2e": e2e,
+                "gpu_launches": r["launches"],
+                "phase_ms_per_step": {"gram": avg[0], "small_solve": avg[1], "update": avg[2]},
+                "status": r["status"]}
+        for arm in arms:
+            if arm != head and results.get(arm):
+                ra = results[arm]
+                line[f"{arm}_arm"] = {"value": ws * args.steps * BATCH / (ra["ms"] * 1e-3),
+                                      "ms_per_step": ra["ms"] / args.steps,
+                                      "phase_ms_per_step": [ra["prof_ms"][i] / max(1, ra["prof_cnt"][i])
+                                                            for i in range(3)]}
+            elif arm != head:
+                line[f"{arm}_arm"] = None
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_sample()
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

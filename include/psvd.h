@@ -155,6 +155,18 @@ int psvd_load(psvd_handle* out, const char* path, void* stream);
 int psvd_gaussian_sketch(uint64_t seed, uint64_t stream_id, int64_t rows, int64_t cols,
                          float* out, void* stream);
 
+/* psvd_set_profiling: enable (1) or disable (0) per-phase CUDA-event timing on
+ * the handle's stream and reset its counters.  Phases: 0 panel Gram (partials
+ * and reduction), 1 small solve (eigen-decomposition, refinement, T), 2 mode
+ * update.  Timing adds two event records per phase and nothing else. */
+int psvd_set_profiling(psvd_handle h, int32_t enable);
+
+/* psvd_get_profile: synchronises, then writes the accumulated device time of
+ * each phase in milliseconds (ms_out[3]), the number of timed executions of each
+ * phase (count_out[3]) and the number of kernels the handle launched since
+ * profiling was enabled (*launches_out).  Any output pointer may be NULL. */
+int psvd_get_profile(psvd_handle h, double* ms_out, int64_t* count_out, int64_t* launches_out);
+
 /* psvd_status_string: static description of a status code. */
 const char* psvd_status_string(int status);
 

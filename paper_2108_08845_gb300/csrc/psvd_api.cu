@@ -13,6 +13,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "psvd_internal.cuh"
 #include "tc_kernels.cuh"
@@ -43,6 +44,17 @@ struct psvd_ctx {
   float* Uf32_tmp = nullptr;  // FP32 view of hi/lo modes for get_modes / save
   int host_info[4] = {0, 0, 0, 0};
   int sticky_status = 0;
+  // per-phase event timing (psvd_set_profiling)
+  bool profiling = false;
+  struct Rec {
+    cudaEvent_t a, b;
+    int phase;
+  };
+  std::vector<Rec> recs;      // recorded, not yet read
+  std::vector<Rec> free_recs; // event pairs available for reuse
+  double prof_ms[3] = {0, 0, 0};
+  int64_t prof_count[3] = {0, 0, 0};
+  int64_t launches = 0;
 };
 
 namespace {
@@ -126,6 +138,42 @@ int ensure_partial(psvd_ctx* h, int64_t doubles) {
 
 bool use_tc(const psvd_ctx* h) { return h->cfg.precision == PSVD_PREC_BF16_TC; }
 
+// Starts timing a phase (returns the record index, or -1 when not profiling).
+int prof_begin(psvd_ctx* h, int phase) {
+  if (!h->profiling) return -1;
+  psvd_ctx::Rec r;
+  if (!h->free_recs.empty()) {
+    r = h->free_recs.back();
+    h->free_recs.pop_back();
+  } else if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  r.phase = phase;
+  cudaEventRecord(r.a, h->st);
+  h->recs.push_back(r);
+  return (int)h->recs.size() - 1;
+}
+
+void prof_end(psvd_ctx* h, int idx) {
+  if (idx >= 0) cudaEventRecord(h->recs[idx].b, h->st);
+}
+
+// Folds completed records into the per-phase totals (synchronises).
+void prof_collect(psvd_ctx* h) {
+  cudaStreamSynchronize(h->st);
+  for (auto& r : h->recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      h->prof_ms[r.phase] += ms;
+      h->prof_count[r.phase] += 1;
+    }
+    cudaGetLastError();
+    h->free_recs.push_back(r);
+  }
+  h->recs.clear();
+}
+
 // Gram of the panel [U | A] (U = current modes, kc columns) -> H = S G S.
 // With G != nullptr the unscaled Gram is stored too.
 int panel_gram(psvd_ctx* h, const void* A, int64_t lda, int B, int dtype, int kc, double ff,
@@ -157,11 +205,19 @@ int step(psvd_ctx* h, const void* A, int64_t lda, int B, int dtype) {
   const int k1 = (h->K < n) ? h->K : n;
   const double* Dcur = h->D[h->cur];
   double* Dnext = h->D[h->cur ^ 1];
+  int pr = prof_begin(h, 0);
   if (int rc = panel_gram(h, A, lda, B, dtype, kc, h->cfg.ff, Dcur, nullptr)) return rc;
+  prof_end(h, pr);
+  h->launches += 2;
   SmallWork w = h->w;
   w.Dnew = Dnext;
+  pr = prof_begin(h, 1);
+  int nl = 0;
   CK(small_solve_launch(w, n, kc, k1, Dcur, h->cfg.ff, /*refine_steps=*/2, /*max_sweeps=*/12,
-                        h->st));
+                        h->st, &nl));
+  prof_end(h, pr);
+  h->launches += nl;
+  pr = prof_begin(h, 2);
   if (use_tc(h)) {
     int rc = tc_update(h->Uh[h->cur], h->Ul[h->cur], h->ldu, kc, A, lda, B, dtype, h->M, w.T3, n,
                        k1, h->Uh[h->cur ^ 1], h->Ul[h->cur ^ 1], h->num_sms, h->st);
@@ -170,6 +226,8 @@ int step(psvd_ctx* h, const void* A, int64_t lda, int B, int dtype) {
     PanelF32 p{h->U[h->cur], h->ldu, kc, A, lda, dtype == PSVD_BF16 ? 1 : 0, h->M, n};
     CK(update_simt_launch(p, w.T, k1, h->U[h->cur ^ 1], h->ldu, h->st));
   }
+  prof_end(h, pr);
+  h->launches += 1;
   h->cur ^= 1;
   h->kc = k1;
   h->iteration += 1;
@@ -293,6 +351,11 @@ int psvd_create(psvd_handle* out, const psvd_config* cfg) {
 void psvd_destroy(psvd_handle h) {
   if (!h) return;
   cudaStreamSynchronize(h->st);
+  for (auto& r : h->recs) h->free_recs.push_back(r);
+  for (auto& r : h->free_recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
   for (int b = 0; b < 2; ++b) {
     cudaFree(h->U[b]);
     cudaFree(h->Uh[b]);
@@ -398,6 +461,29 @@ int psvd_parallel_svd(psvd_handle h, const void* A, int64_t lda, const int64_t* 
   (void)U_out; (void)ldu; (void)L_out;
   if (!h) return PSVD_ERR_INVALID_ARG;
   return PSVD_ERR_UNSUPPORTED;
+}
+
+int psvd_set_profiling(psvd_handle h, int32_t enable) {
+  if (!h) return PSVD_ERR_INVALID_ARG;
+  prof_collect(h);
+  h->profiling = enable != 0;
+  for (int i = 0; i < 3; ++i) {
+    h->prof_ms[i] = 0.0;
+    h->prof_count[i] = 0;
+  }
+  h->launches = 0;
+  return PSVD_OK;
+}
+
+int psvd_get_profile(psvd_handle h, double* ms_out, int64_t* count_out, int64_t* launches_out) {
+  if (!h) return PSVD_ERR_INVALID_ARG;
+  prof_collect(h);
+  for (int i = 0; i < 3; ++i) {
+    if (ms_out) ms_out[i] = h->prof_ms[i];
+    if (count_out) count_out[i] = h->prof_count[i];
+  }
+  if (launches_out) *launches_out = h->launches;
+  return PSVD_OK;
 }
 
 int psvd_gaussian_sketch(uint64_t seed, uint64_t stream_id, int64_t rows, int64_t cols, float* out,

@@ -68,8 +68,10 @@ struct SmallWork {
 // Eigen-decomposition of H (n x n) and the update coefficients:
 //   H = X diag(lam) X^T (descending), sigma = sqrt(lam[0:k1]),
 //   T = S X[:, 0:k1] diag(1/sigma), Dnew = sigma.
+// *launches receives the number of kernels enqueued.
 cudaError_t small_solve_launch(const SmallWork& w, int n, int kc, int k1, const double* D,
-                               double ff, int refine_steps, int max_sweeps, cudaStream_t st);
+                               double ff, int refine_steps, int max_sweeps, cudaStream_t st,
+                               int* launches);
 // FP64 Cholesky R^T R = G (n x n) into R (ld n, upper); info[2] = status.
 cudaError_t cholesky_launch(const double* G, int n, double* R, int* info, cudaStream_t st);
 

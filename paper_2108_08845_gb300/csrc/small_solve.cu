@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(JT) jacobi_eig_kernel(const double* __restrict
   extern __shared__ __align__(16) float sm[];
   __shared__ float cs_c[kMaxN / 2], cs_s[kMaxN / 2];
   __shared__ int pp[kMaxN / 2], qq[kMaxN / 2];
-  __shared__ int rot_any;
+  __shared__ int rot_any, rot_round;
   __shared__ int rank_of[kMaxN];
   const int N = (n + 1) & ~1;
   const int P = N / 2;
@@ -77,6 +77,8 @@ __global__ void __launch_bounds__(JT) jacobi_eig_kernel(const double* __restrict
     if (tid == 0) rot_any = 0;
     __syncthreads();
     for (int r = 0; r < N - 1; ++r) {
+      if (tid == 0) rot_round = 0;
+      __syncthreads();
       // rotation of each disjoint pair (p, q): zeroes H_pq (Golub & Van Loan sym.schur2)
       if (tid < P) {
         int p = tour_player(tid, r, N), q = tour_player(N - 1 - tid, r, N);
@@ -94,6 +96,7 @@ __global__ void __launch_bounds__(JT) jacobi_eig_kernel(const double* __restrict
           Hp[pidx(q, q)] = aqq + t * apq;
           Hp[pidx(p, q)] = 0.f;
           rot_any = 1;
+          rot_round = 1;
         }
         pp[tid] = p;
         qq[tid] = q;
@@ -101,6 +104,9 @@ __global__ void __launch_bounds__(JT) jacobi_eig_kernel(const double* __restrict
         cs_s[tid] = s;
       }
       __syncthreads();
+      if (!rot_round) {  // no pair rotated in this round: nothing to apply
+        continue;
+      }
       // off-diagonal 2x2 blocks: B_kl <- J_k^T B_kl J_l (each entry in one block)
       for (int e = tid; e < P * P; e += JT) {
         const int k = e / P, l = e % P;
@@ -349,19 +355,24 @@ size_t jacobi_smem_bytes(int n) {
 }
 
 cudaError_t small_solve_launch(const SmallWork& w, int n, int kc, int k1, const double* D,
-                               double ff, int refine_steps, int max_sweeps, cudaStream_t st) {
+                               double ff, int refine_steps, int max_sweeps, cudaStream_t st,
+                               int* launches) {
+  *launches = 5 + 6 * refine_steps + (refine_steps == 0 ? 1 : 0) + 1;
   const size_t smem = jacobi_smem_bytes(n);
   cudaError_t e = cudaFuncSetAttribute(jacobi_eig_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   // stage 1: FP32 Jacobi on H -> X1 (in E), eigenvalues (in lamJ, unused)
-  const int stage1_sweeps = (max_sweeps < 8) ? max_sweeps : 8;
+  // stage 1 stalls at the FP32 rounding floor after a handful of sweeps
+  const int stage1_sweeps = (max_sweeps < 5) ? max_sweeps : 5;
   jacobi_eig_kernel<<<1, JT, smem, st>>>(w.H, n, w.E, w.lamJ, stage1_sweeps, 2e-6f, w.info, 0, 0);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // stage 2: H2 = X1^T H X1 (FP64, in S), FP32 Jacobi on H2 -> X2 (in R), lam
   if ((e = dgemm<false>(n, n, n, 1.0, w.H, n, w.E, n, 0.0, nullptr, n, w.W, n, st))) return e;
   if ((e = dgemm<true>(n, n, n, 1.0, w.E, n, w.W, n, 0.0, nullptr, n, w.S, n, st))) return e;
-  jacobi_eig_kernel<<<1, JT, smem, st>>>(w.S, n, w.R, w.lam, max_sweeps, 2e-6f, w.info, 1, 1);
+  // stage 2 stops at relative off-diagonals of 1e-4: the FP64 refinement that
+  // follows is quadratically convergent from there
+  jacobi_eig_kernel<<<1, JT, smem, st>>>(w.S, n, w.R, w.lam, max_sweeps, 1e-4f, w.info, 1, 1);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // X = X1 X2
   if ((e = dgemm<false>(n, n, n, 1.0, w.E, n, w.R, n, 0.0, nullptr, n, w.X, n, st))) return e;

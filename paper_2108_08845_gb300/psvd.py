@@ -89,6 +89,9 @@ def load(build_if_missing: bool = True):
         lib.psvd_status_string.argtypes = [C.c_int]
         lib.psvd_status_string.restype = C.c_char_p
         lib.psvd_last_info.argtypes = [vp, C.POINTER(C.c_int32)]
+        lib.psvd_set_profiling.argtypes = [vp, i32]
+        lib.psvd_get_profile.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64),
+                                         C.POINTER(C.c_int64)]
         _lib = lib
         return lib
 
@@ -236,6 +239,19 @@ def psvd_last_info(h: int):
     info = (C.c_int32 * 4)()
     rc = _check(load().psvd_last_info(h, info), "psvd_last_info")
     return rc, [int(x) for x in info]
+
+
+def psvd_set_profiling(h: int, enable: bool) -> int:
+    return _check(load().psvd_set_profiling(h, 1 if enable else 0), "psvd_set_profiling")
+
+
+def psvd_get_profile(h: int):
+    """(ms[3], counts[3], launches): per-phase device time (Gram, small solve, update)."""
+    ms = (C.c_double * 3)()
+    cnt = (C.c_int64 * 3)()
+    nl = C.c_int64()
+    _check(load().psvd_get_profile(h, ms, cnt, C.byref(nl)), "psvd_get_profile")
+    return [float(x) for x in ms], [int(x) for x in cnt], int(nl.value)
 
 
 class StreamingSVD:
