@@ -14,7 +14,10 @@
  *     contiguous.
  *   - Data pointers may be device pointers or host pointers (pageable or
  *     pinned); the library detects which with cudaPointerGetAttributes.  Host
- *     inputs are staged through a device buffer owned by the handle.
+ *     inputs are staged through a device buffer owned by the handle.  On the
+ *     tensor-core path, device inputs whose base address or leading dimension
+ *     (in bytes) is not a multiple of 16 are also re-staged (one extra copy);
+ *     aligned inputs are read in place.
  *   - Work is enqueued on the handle's CUDA stream.  Calls that return data to
  *     the caller (psvd_get_*, psvd_parallel_qr, psvd_parallel_svd) synchronise
  *     that stream before returning.  Calls that only consume inputs
@@ -51,6 +54,8 @@ extern "C" {
 #define PSVD_ERR_ALLOC -6            /* device or host allocation failed */
 #define PSVD_ERR_IO -7               /* psvd_save / psvd_load file error or bad format */
 #define PSVD_ERR_UNSUPPORTED -8      /* feature not available for this precision/shape */
+#define PSVD_ERR_TIMEOUT -9          /* a device-side wait exceeded its time budget; the
+                                        kernel abandoned its work (results are invalid) */
 
 /* ----------------------------------------------------------------- enums */
 typedef enum {
@@ -74,7 +79,9 @@ typedef enum {
 typedef struct {
   int64_t M;          /* rows (grid points) of every snapshot, >= 1 */
   int32_t K;          /* modes kept after every batch (Alg. 1 steps 3 and 5), >= 1 */
-  int32_t max_batch;  /* largest snapshot count B per call; K + max_batch <= 192 */
+  int32_t max_batch;  /* largest snapshot count B per call; K + max_batch <= 192;
+                         PSVD_PREC_BF16_TC also needs K <= 80 and
+                         2*roundup(K,8) + roundup(max_batch,8) <= 256 */
   double ff;          /* forget factor in (0, 1] (Sec. 3.1): scales U*D, i.e. sigma */
   int32_t precision;  /* psvd_precision */
   int32_t low_rank;   /* 1: the SVD of each panel is the randomized low-rank SVD

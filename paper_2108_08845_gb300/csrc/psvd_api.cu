@@ -94,16 +94,22 @@ int dalloc(T** p, size_t count) {
   return PSVD_OK;
 }
 
-// Device copy of a column-major input (staged if it lives in host memory).
+// Device copy of a column-major input: host inputs are staged; with align16 (the
+// tensor-core path, whose TMA copies need 16-byte aligned columns) device inputs
+// whose base or leading dimension is not 16-byte aligned are re-staged with a
+// padded leading dimension.
 int stage_input(psvd_ctx* h, const void* A, int64_t lda, int64_t rows, int cols, int dtype,
-                const void** dev, int64_t* ld_dev) {
-  if (is_device_ptr(A)) {
+                bool align16, const void** dev, int64_t* ld_dev) {
+  const size_t es = (size_t)elem_size(dtype);
+  const bool on_dev = is_device_ptr(A);
+  const bool aligned = (((uintptr_t)A & 15) == 0) && (((size_t)lda * es) % 16 == 0);
+  if (on_dev && (!align16 || aligned)) {
     *dev = A;
     *ld_dev = lda;
     return PSVD_OK;
   }
-  const size_t es = (size_t)elem_size(dtype);
-  const size_t need = es * (size_t)rows * (size_t)cols;
+  const int64_t ld = align16 ? ceil_div(rows, 8) * 8 : rows;
+  const size_t need = es * (size_t)ld * (size_t)cols;
   if (need > h->staging_bytes) {
     if (h->staging) {
       CK(cudaStreamSynchronize(h->st));
@@ -117,10 +123,10 @@ int stage_input(psvd_ctx* h, const void* A, int64_t lda, int64_t rows, int cols,
     }
     h->staging_bytes = need;
   }
-  CK(cudaMemcpy2DAsync(h->staging, es * rows, A, es * lda, es * rows, cols, cudaMemcpyHostToDevice,
-                       h->st));
+  CK(cudaMemcpy2DAsync(h->staging, es * ld, A, es * lda, es * rows, cols,
+                       on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
   *dev = h->staging;
-  *ld_dev = rows;
+  *ld_dev = ld;
   return PSVD_OK;
 }
 
@@ -181,9 +187,10 @@ int panel_gram(psvd_ctx* h, const void* A, int64_t lda, int B, int dtype, int kc
   const int n = kc + B;
   if (use_tc(h)) {
     int rc = tc_gram(h->Uh[h->cur], h->Ul[h->cur], h->ldu, kc, A, lda, B, dtype, h->M, h->num_sms,
-                     &h->partial, &h->partial_cap, h->st);
+                     &h->partial, &h->partial_cap, &h->w.info[2], h->st);
     if (rc) return rc;
-    return tc_gram_reduce(h->partial, h->M, kc, B, h->num_sms, ff, D, G, h->w.H, h->st)
+    return tc_gram_reduce(h->partial, h->M, kc, B, h->num_sms, ff, D, G, h->w.H, &h->w.info[2],
+                          h->st)
                ? PSVD_ERR_CUDA
                : PSVD_OK;
   }
@@ -208,7 +215,7 @@ int step(psvd_ctx* h, const void* A, int64_t lda, int B, int dtype) {
   int pr = prof_begin(h, 0);
   if (int rc = panel_gram(h, A, lda, B, dtype, kc, h->cfg.ff, Dcur, nullptr)) return rc;
   prof_end(h, pr);
-  h->launches += 2;
+  h->launches += use_tc(h) ? 3 : 2;
   SmallWork w = h->w;
   w.Dnew = Dnext;
   pr = prof_begin(h, 1);
@@ -219,15 +226,16 @@ int step(psvd_ctx* h, const void* A, int64_t lda, int B, int dtype) {
   h->launches += nl;
   pr = prof_begin(h, 2);
   if (use_tc(h)) {
-    int rc = tc_update(h->Uh[h->cur], h->Ul[h->cur], h->ldu, kc, A, lda, B, dtype, h->M, w.T3, n,
-                       k1, h->Uh[h->cur ^ 1], h->Ul[h->cur ^ 1], h->num_sms, h->st);
+    int rc = tc_update(h->Uh[h->cur], h->Ul[h->cur], h->ldu, kc, A, lda, B, dtype, h->M, w.T, n,
+                       k1, w.T3, h->Uh[h->cur ^ 1], h->Ul[h->cur ^ 1], h->num_sms, &h->w.info[2],
+                       h->st);
     if (rc) return rc;
   } else {
     PanelF32 p{h->U[h->cur], h->ldu, kc, A, lda, dtype == PSVD_BF16 ? 1 : 0, h->M, n};
     CK(update_simt_launch(p, w.T, k1, h->U[h->cur ^ 1], h->ldu, h->st));
   }
   prof_end(h, pr);
-  h->launches += 1;
+  h->launches += use_tc(h) ? 2 : 1;
   h->cur ^= 1;
   h->kc = k1;
   h->iteration += 1;
@@ -248,6 +256,7 @@ int collect_status(psvd_ctx* h) {
   CK(cudaMemcpyAsync(h->host_info, h->w.info, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
   const int bits = h->host_info[2];
+  if (bits & 8) h->sticky_status = PSVD_ERR_TIMEOUT;
   if (bits & 4) h->sticky_status = PSVD_ERR_NONFINITE;
   if (h->sticky_status < 0) return h->sticky_status;
   if (bits & 1) return PSVD_WARN_RANK_DEFICIENT;
@@ -272,6 +281,7 @@ const char* psvd_status_string(int s) {
     case PSVD_ERR_ALLOC: return "allocation failed";
     case PSVD_ERR_IO: return "file I/O error or bad file";
     case PSVD_ERR_UNSUPPORTED: return "unsupported for this precision or configuration";
+    case PSVD_ERR_TIMEOUT: return "a device-side wait timed out (kernel aborted its work)";
     default: return "unknown status";
   }
 }
@@ -284,6 +294,9 @@ int psvd_create(psvd_handle* out, const psvd_config* cfg) {
   if (cfg->precision != PSVD_PREC_FP32 && cfg->precision != PSVD_PREC_BF16_TC)
     return PSVD_ERR_INVALID_ARG;
   if ((int64_t)cfg->K + cfg->max_batch > kMaxN) return PSVD_ERR_SHAPE;
+  if (cfg->precision == PSVD_PREC_BF16_TC &&
+      (cfg->K > 80 || ((2 * ((cfg->K + 7) & ~7) + ((cfg->max_batch + 7) & ~7) + 15) & ~15) > 256))
+    return PSVD_ERR_SHAPE;
   if (cfg->low_rank) return PSVD_ERR_UNSUPPORTED;
   psvd_ctx* h = new (std::nothrow) psvd_ctx();
   if (!h) return PSVD_ERR_ALLOC;
@@ -324,7 +337,7 @@ int psvd_create(psvd_handle* out, const psvd_config* cfg) {
   if (!rc) rc = dalloc(&h->w.Xn, nm * nm);
   if (!rc) rc = dalloc(&h->w.lamJ, nm);
   if (!rc) rc = dalloc(&h->w.T, nm * (size_t)h->K);
-  if (!rc) rc = dalloc(&h->w.T3, 3 * nm * (size_t)h->K);
+  if (!rc) rc = dalloc(&h->w.T3, tc_t3_elems(h->K, h->maxB));
   if (!rc) rc = dalloc(&h->w.info, 4);
   if (!rc && cudaMemsetAsync(h->w.info, 0, sizeof(int) * 4, h->st) != cudaSuccess) rc = PSVD_ERR_CUDA;
   if (!rc) {
@@ -388,7 +401,7 @@ int psvd_initialize(psvd_handle h, const void* A0, int64_t lda, int32_t B, int32
   if (int rc = check_batch(h, A0, lda, B, dtype)) return rc;
   const void* Ad;
   int64_t ldd;
-  if (int rc = stage_input(h, A0, lda, h->M, B, dtype, &Ad, &ldd)) return rc;
+  if (int rc = stage_input(h, A0, lda, h->M, B, dtype, use_tc(h), &Ad, &ldd)) return rc;
   CK(cudaMemsetAsync(h->w.info, 0, sizeof(int) * 4, h->st));
   h->sticky_status = 0;
   h->iteration = 0;
@@ -401,7 +414,7 @@ int psvd_incorporate_data(psvd_handle h, const void* A, int64_t lda, int32_t B, 
   if (int rc = check_batch(h, A, lda, B, dtype)) return rc;
   const void* Ad;
   int64_t ldd;
-  if (int rc = stage_input(h, A, lda, h->M, B, dtype, &Ad, &ldd)) return rc;
+  if (int rc = stage_input(h, A, lda, h->M, B, dtype, use_tc(h), &Ad, &ldd)) return rc;
   return step(h, Ad, ldd, B, dtype);
 }
 
@@ -443,7 +456,7 @@ int psvd_parallel_qr(psvd_handle h, const void* P, int64_t ldp, int32_t n, int32
   if (use_tc(h) && dtype != PSVD_BF16) return PSVD_ERR_UNSUPPORTED;
   const void* Pd;
   int64_t ldd;
-  if (int rc = stage_input(h, P, ldp, h->M, n, dtype, &Pd, &ldd)) return rc;
+  if (int rc = stage_input(h, P, ldp, h->M, n, dtype, use_tc(h), &Pd, &ldd)) return rc;
   CK(cudaMemsetAsync(h->w.info, 0, sizeof(int) * 4, h->st));
   if (int rc = panel_gram(h, Pd, ldd, n, dtype, 0, 1.0, h->D[h->cur], h->G)) return rc;
   CK(cholesky_launch(h->G, n, h->w.X, h->w.info, h->st));

@@ -395,7 +395,7 @@ cudaError_t small_solve_launch(const SmallWork& w, int n, int kc, int k1, const 
     copy_cols_kernel<<<(unsigned)ceil_div(cnt, 256), 256, 0, st>>>(w.lam, w.lamJ, cnt);
     if ((e = cudaGetLastError())) return e;
   }
-  finalize_kernel<<<1, 256, 0, st>>>(n, nJ, kc, k1, w.X, w.lamJ, D, ff, w.T, w.T3, w.Dnew, w.info);
+  finalize_kernel<<<1, 256, 0, st>>>(n, nJ, kc, k1, w.X, w.lamJ, D, ff, w.T, nullptr, w.Dnew, w.info);
   return cudaGetLastError();
 }
 

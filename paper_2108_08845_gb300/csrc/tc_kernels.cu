@@ -1,25 +1,796 @@
-// Placeholder until the tcgen05 kernels land: the BF16 tensor-core path reports
-// PSVD_ERR_UNSUPPORTED.
+// tcgen05 tensor-core kernels of the BF16 path of the per-batch update of
+// Algorithm 1 (Sec. 3.1).
+//
+// The modes are stored as a pair of BF16 planes, U = Uh + Ul (16 significant
+// bits), the snapshots A in BF16, so the padded panel
+//     P' = [Uh (kcp cols) | Ul (kcp cols) | A (Bp cols)],  kcp = roundup(kc, 8)
+// is an exact BF16 representation of [U | A] and every product on the tensor
+// cores is exact; accumulation is FP32 in tensor memory (TMEM).
+//
+// tc_gram_kernel: the panel Gram P'^T P' (step 1's R^T R).  P' is streamed in
+//   64-row stages by TMA (SWIZZLE_128B, each column one 128-byte row, i.e. the
+//   K-major canonical layout with K = rows); for every pair of 128-column slabs
+//   (i <= j) one tcgen05.mma per 16 rows accumulates slab_i^T slab_j into TMEM.
+//   A row chunk's accumulators are drained by four epilogue warps to FP32
+//   partials in global memory, summed in FP64 in a fixed order by
+//   tc_gram_reduce_kernel, which also folds Uh/Ul back into U.
+// tc_update_kernel: step 4, U_new = [U | A] T.  T (n x k1, FP32) is split
+//   exactly into three BF16 parts, so one MMA with N = 3 * k1p computes the
+//   three partial products; P' row tiles of 128 rows are the MN-major A operand
+//   (the same TMA layout, two 64-row halves), T3 the K-major B operand resident
+//   in shared memory.  Two TMEM accumulators alternate so the epilogue (sum of
+//   the three parts, hi/lo split, stores) overlaps the next tile's MMAs.
+//
+// Warp roles (both kernels): warp 0 issues TMA loads, warp 1 allocates TMEM
+// and issues MMAs (one elected thread), warps 2-5 drain TMEM (warp w reads the
+// TMEM lanes 32*(w%4) .. 32*(w%4)+31).  Every mbarrier wait is bounded by a
+// clock budget; on expiry the kernel records an error, stops issuing work,
+// waits (bounded) for its own copies and frees its TMEM before returning.
+#include <cuda.h>
+#include <stdio.h>
+
 #include "tc_kernels.cuh"
 
 namespace psvd {
+namespace {
 
-int tc_gram(const __nv_bfloat16*, const __nv_bfloat16*, int64_t, int, const void*, int64_t, int,
-            int, int64_t, int, double**, int64_t*, cudaStream_t) {
-  return PSVD_ERR_UNSUPPORTED;
+constexpr int kRowsStage = 64;            // rows per Gram stage (one 128-byte swizzle row per column)
+constexpr int kSlab = 128;                // panel columns per MMA slab (UMMA M)
+constexpr int kGramStages = 6;
+constexpr int kUpdRows = 128;             // rows per update tile (UMMA M)
+constexpr int kUpdStages = 2;
+constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
-cudaError_t tc_gram_reduce(const double*, int64_t, int, int, int, double, const double*, double*,
-                           double*, cudaStream_t) {
-  return cudaErrorNotSupported;
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }
-int tc_update(const __nv_bfloat16*, const __nv_bfloat16*, int64_t, int, const void*, int64_t, int,
-              int, int64_t, const __nv_bfloat16*, int, int, __nv_bfloat16*, __nv_bfloat16*, int,
-              cudaStream_t) {
-  return PSVD_ERR_UNSUPPORTED;
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
 }
-cudaError_t tc_modes_to_f32(const __nv_bfloat16*, const __nv_bfloat16*, int64_t, int64_t, int,
-                            float*, cudaStream_t) {
-  return cudaErrorNotSupported;
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait on phase `parity`; on expiry sets *abort and the error word.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                          int* err) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      *abort = 1;
+      atomicOr(err, 8);  // err points at the handle's status word
+      return false;
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst, int x,
+                                            int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(dst)),
+               "r"(ncols));
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+// 32 consecutive TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor, SWIZZLE_128B (layout type 2), version 1.
+//   K-major:  rows of 128 bytes (64 bf16 along K), 8-row groups SBO = 1024 bytes.
+//   MN-major: rows of 128 bytes (64 bf16 along M/N) per K index, 8 K indices per
+//             1024-byte atom (SBO), LBO = stride between 64-element M/N atoms.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo_bytes, uint32_t sbo_bytes) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo_bytes >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo_bytes >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version (sm_100 family)
+  d |= (uint64_t)2 << 61;  // SWIZZLE_128B
+  return d;
+}
+// Instruction descriptor of kind::f16: BF16 x BF16 -> FP32, M = 128.
+__host__ __device__ constexpr uint32_t idesc_bf16(int N, int a_mn_major, int b_mn_major) {
+  return (1u << 4)                        // D format: F32
+         | (1u << 7)                      // A format: BF16
+         | (1u << 10)                     // B format: BF16
+         | ((uint32_t)a_mn_major << 15)   // A major-ness (0: K-major, 1: MN-major)
+         | ((uint32_t)b_mn_major << 16)   // B major-ness
+         | ((uint32_t)(N >> 3) << 17)     // N / 8
+         | ((uint32_t)(128 >> 4) << 24);  // M / 16
+}
+
+struct GramGeom {
+  int64_t M;
+  int kcp;     // padded mode columns per plane (multiple of 8), 0 at initialisation
+  int Bp;      // padded snapshot columns (multiple of 8)
+  int np;      // 2*kcp + Bp
+  int nslab;   // ceil(np / 128)
+  int npair;   // nslab*(nslab+1)/2
+  int64_t chunk_rows;  // rows per accumulation chunk (multiple of 64)
+  int64_t nchunk;
+};
+
+__device__ __forceinline__ void pair_of(int p, int nslab, int* i, int* j) {
+  int a = 0;
+  while (p >= nslab - a) {
+    p -= nslab - a;
+    ++a;
+  }
+  *i = a;
+  *j = a + p;
+}
+
+__device__ __forceinline__ int slab_width16(int s, int np) {
+  const int w = min(kSlab, np - s * kSlab);
+  return (w + 15) & ~15;
+}
+
+// partial layout: [chunk][pair][128 lanes][128 columns] FP32
+__global__ void __launch_bounds__(192, 1) tc_gram_kernel(const __grid_constant__ CUtensorMap mUh,
+                                                         const __grid_constant__ CUtensorMap mUl,
+                                                         const __grid_constant__ CUtensorMap mA,
+                                                         GramGeom g, float* __restrict__ partial,
+                                                         int* __restrict__ err) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  // 1024-byte aligned stage buffers (SWIZZLE_128B atoms)
+  uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int stage_bytes = g.nslab * kSlab * 128;
+  uint8_t* stages = base;
+  uint64_t* full = (uint64_t*)(stages + (size_t)kGramStages * stage_bytes);
+  uint64_t* empty = full + kGramStages;
+  uint64_t* acc_full = empty + kGramStages;
+  uint64_t* acc_empty = acc_full + 1;
+  uint64_t* mma_done = acc_empty + 1;
+  uint32_t* tmem_slot = (uint32_t*)(mma_done + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ktiles = (int)(g.chunk_rows / kRowsStage);
+  const uint32_t tx_bytes = (uint32_t)(2 * g.kcp + g.Bp) * 128u;
+
+  // zero the stage buffers once: columns beyond np inside the last slab stay zero
+  for (int i = threadIdx.x; i < kGramStages * stage_bytes / 16; i += blockDim.x)
+    reinterpret_cast<int4*>(stages)[i] = make_int4(0, 0, 0, 0);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kGramStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, 4);
+    mbar_init(mma_done, 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  fence_proxy_async_smem();
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------------------------------------------------- TMA producer
+      int stage = 0;
+      uint32_t phase = 0;
+      int issued = 0;
+      for (int64_t c = blockIdx.x; c < g.nchunk && !*abort_flag; c += gridDim.x) {
+        for (int kt = 0; kt < ktiles; ++kt) {
+          const int64_t row = c * g.chunk_rows + (int64_t)kt * kRowsStage;
+          if (row >= g.M) break;
+          if (issued >= kGramStages && !mbar_wait(&empty[stage], phase ^ 1, abort_flag, err)) break;
+          uint8_t* dst = stages + (size_t)stage * stage_bytes;
+          mbar_expect_tx(&full[stage], tx_bytes);
+          if (g.kcp > 0) {
+            tma_load_2d(&mUh, &full[stage], dst, (int)row, 0);
+            tma_load_2d(&mUl, &full[stage], dst + g.kcp * 128, (int)row, 0);
+          }
+          tma_load_2d(&mA, &full[stage], dst + 2 * g.kcp * 128, (int)row, 0);
+          ++issued;
+          if (++stage == kGramStages) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+        if (*abort_flag) break;
+      }
+      // drain: wait (bounded) until the in-flight copies have landed
+      const int inflight = issued < kGramStages ? issued : kGramStages;
+      for (int i = 0; i < inflight; ++i) {
+        if (--stage < 0) {
+          stage = kGramStages - 1;
+          phase ^= 1;
+        }
+        const long long t0 = clock64();
+        while (!mbar_try_wait(&full[stage], phase) && clock64() - t0 < kWaitCycles) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // --------------------------------------------------------- MMA issuer
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t acc_phase = 0;
+      bool first_chunk = true;
+      for (int64_t c = blockIdx.x; c < g.nchunk; c += gridDim.x) {
+        if (!first_chunk && !mbar_wait(acc_empty, acc_phase ^ 1, abort_flag, err)) break;
+        first_chunk = false;
+        bool ok = true;
+        int kt = 0;
+        for (; kt < ktiles; ++kt) {
+          const int64_t row = c * g.chunk_rows + (int64_t)kt * kRowsStage;
+          if (row >= g.M) break;
+          if (!mbar_wait(&full[stage], phase, abort_flag, err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sbase = smem_u32(stages + (size_t)stage * stage_bytes);
+#pragma unroll 1
+          for (int p = 0; p < g.npair; ++p) {
+            int si, sj;
+            pair_of(p, g.nslab, &si, &sj);
+            const uint32_t idesc = idesc_bf16(slab_width16(sj, g.np), 0, 0);
+            const uint32_t d_tmem = tmem_base + (uint32_t)(p * kSlab);
+#pragma unroll
+            for (int k = 0; k < kRowsStage / 16; ++k) {
+              const uint64_t ad = smem_desc(sbase + si * kSlab * 128 + k * 32, 16, 1024);
+              const uint64_t bd = smem_desc(sbase + sj * kSlab * 128 + k * 32, 16, 1024);
+              umma_bf16(d_tmem, ad, bd, idesc, (kt > 0 || k > 0) ? 1u : 0u);
+            }
+          }
+          umma_commit(&empty[stage]);  // frees the stage when these MMAs complete
+          if (++stage == kGramStages) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+        if (!ok) break;
+        umma_commit(acc_full);  // chunk accumulated
+        acc_phase ^= 1;
+      }
+      // every issued MMA has completed before TMEM is released
+      umma_commit(mma_done);
+      const long long t0 = clock64();
+      while (!mbar_try_wait(mma_done, 0) && clock64() - t0 < kWaitCycles) {
+      }
+    }
+  } else {
+    // ------------------------------------------------------------- epilogue
+    const int sub = warp & 3;  // TMEM sub-partition of this warp
+    const int row_in_slab = sub * 32 + lane;
+    uint32_t acc_phase = 0;
+    for (int64_t c = blockIdx.x; c < g.nchunk; c += gridDim.x) {
+      if (!mbar_wait(acc_full, acc_phase, abort_flag, err)) break;
+      acc_phase ^= 1;
+      tc_fence_after();
+      float* out = partial + (size_t)c * g.npair * kSlab * kSlab;
+      for (int p = 0; p < g.npair; ++p) {
+        int si, sj;
+        pair_of(p, g.nslab, &si, &sj);
+        const int w = slab_width16(sj, g.np);
+        float* orow = out + ((size_t)p * kSlab + row_in_slab) * kSlab;
+        for (int c0 = 0; c0 < w; c0 += 32) {
+          float v[32];
+          tmem_ld32(tmem_base + ((uint32_t)(sub * 32) << 16) + (uint32_t)(p * kSlab + c0), v);
+#pragma unroll
+          for (int i = 0; i < 32; i += 4)
+            if (c0 + i < w) *reinterpret_cast<float4*>(&orow[c0 + i]) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+        }
+      }
+      tc_fence_before();
+      if (lane == 0) mbar_arrive(acc_empty);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem_base, 512);
+}
+
+// Ssum[pair][x][y] = sum over chunks of the FP32 partials, in FP64, chunk order fixed.
+__global__ void tc_gram_sum_kernel(const float* __restrict__ partial, int64_t nchunk, int npair,
+                                   double* __restrict__ Ssum) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t per = (int64_t)npair * kSlab * kSlab;
+  if (e >= per) return;
+  double s = 0.0;
+  for (int64_t c = 0; c < nchunk; ++c) s += (double)partial[c * per + e];
+  Ssum[e] = s;
+}
+
+// G (n x n, logical columns [U (kc) | A (B)]) from Ssum; H = S G S.  A mode
+// column of U appears twice in the padded panel (hi and lo plane); its Gram
+// entries are the sums over both.
+__global__ void tc_gram_assemble_kernel(const double* __restrict__ Ssum, GramGeom g, int kc, int B,
+                                        const double* __restrict__ D, double ff,
+                                        double* __restrict__ G, double* __restrict__ H,
+                                        int* __restrict__ status) {
+  const int n = kc + B;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * n) return;
+  const int i = (int)(e % n), j = (int)(e / n);
+  if (i > j) return;  // computed once, mirrored
+  int ci[2], cj[2], ni, nj;
+  if (i < kc) { ci[0] = i; ci[1] = g.kcp + i; ni = 2; } else { ci[0] = 2 * g.kcp + (i - kc); ni = 1; }
+  if (j < kc) { cj[0] = j; cj[1] = g.kcp + j; nj = 2; } else { cj[0] = 2 * g.kcp + (j - kc); nj = 1; }
+  double s = 0.0;
+  for (int a = 0; a < ni; ++a)
+    for (int b = 0; b < nj; ++b) {
+      int x = ci[a], y = cj[b];
+      if (x / kSlab > y / kSlab) { const int tmp = x; x = y; y = tmp; }
+      const int sx = x / kSlab, sy = y / kSlab;
+      const int p = sx * g.nslab - sx * (sx - 1) / 2 + (sy - sx);
+      s += Ssum[((size_t)p * kSlab + (x % kSlab)) * kSlab + (y % kSlab)];
+    }
+  const double si = (i < kc) ? ff * D[i] : 1.0;
+  const double sj = (j < kc) ? ff * D[j] : 1.0;
+  if (G) {
+    G[i + (int64_t)j * n] = s;
+    G[j + (int64_t)i * n] = s;
+  }
+  H[i + (int64_t)j * n] = si * sj * s;
+  H[j + (int64_t)i * n] = si * sj * s;
+  if (!isfinite(s)) atomicOr(status, 4);
+}
+
+struct UpdGeom {
+  int64_t M;
+  int kcp, Bp, np;  // padded panel (as in the Gram)
+  int k1, k1p;      // kept modes, padded to 16
+  int N;            // 3 * k1p
+  int nkb;          // K blocks of 64 panel columns: ceil(np / 64)
+  int64_t ntiles;   // row tiles of 128
+  int64_t ldu;
+};
+
+// T3 (N x npk row-major BF16, npk = 64 * nkb): row part*k1p + j, column = padded
+// panel column; the value is the part-th BF16 term of T[logical col][j].
+__global__ void tc_pack_T_kernel(const float* __restrict__ T, int n, int kc, UpdGeom u, int npk,
+                                 __nv_bfloat16* __restrict__ T3) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)u.N * npk) return;
+  const int col = (int)(e % npk), row = (int)(e / npk);
+  const int part = row / u.k1p, j = row % u.k1p;
+  int lc = -1;  // logical panel column
+  if (col < u.kcp) lc = (col < kc) ? col : -1;
+  else if (col < 2 * u.kcp) lc = (col - u.kcp < kc) ? col - u.kcp : -1;
+  else if (col - 2 * u.kcp < n - kc) lc = kc + (col - 2 * u.kcp);
+  float v = 0.f;
+  if (lc >= 0 && j < u.k1) {
+    const float t = T[lc + (int64_t)j * n];
+    const __nv_bfloat16 h = __float2bfloat16_rn(t);
+    const float r1 = t - __bfloat162float(h);
+    const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(m);
+    v = part == 0 ? __bfloat162float(h) : part == 1 ? __bfloat162float(m) : r2;
+  }
+  T3[e] = __float2bfloat16_rn(v);
+}
+
+__global__ void __launch_bounds__(192, 1) tc_update_kernel(const __grid_constant__ CUtensorMap mUh,
+                                                           const __grid_constant__ CUtensorMap mUl,
+                                                           const __grid_constant__ CUtensorMap mA,
+                                                           const __grid_constant__ CUtensorMap mT,
+                                                           UpdGeom u, __nv_bfloat16* __restrict__ Uh_new,
+                                                           __nv_bfloat16* __restrict__ Ul_new,
+                                                           int* __restrict__ err) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int half_bytes = u.np * 128;         // one 64-row half of a tile
+  const int stage_bytes = 2 * half_bytes;    // 128 rows
+  const int tb_bytes = u.N * 128;            // one 64-column K block of T3
+  uint8_t* stages = base;
+  uint8_t* tsm = stages + (size_t)kUpdStages * stage_bytes;
+  uint64_t* full = (uint64_t*)(tsm + (size_t)u.nkb * tb_bytes);
+  uint64_t* empty = full + kUpdStages;
+  uint64_t* t_full = empty + kUpdStages;
+  uint64_t* acc_full = t_full + 1;   // [2]
+  uint64_t* acc_empty = acc_full + 2;  // [2]
+  uint64_t* mma_done = acc_empty + 2;
+  uint32_t* tmem_slot = (uint32_t*)(mma_done + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kUpdStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(t_full, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);
+    }
+    mbar_init(mma_done, 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const uint32_t tx_bytes = (uint32_t)stage_bytes;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // T3 once (K blocks of 64 columns, N rows each)
+      mbar_expect_tx(t_full, (uint32_t)(u.nkb * tb_bytes));
+      for (int kb = 0; kb < u.nkb; ++kb) tma_load_2d(&mT, t_full, tsm + (size_t)kb * tb_bytes, kb * 64, 0);
+      int stage = 0, issued = 0;
+      uint32_t phase = 0;
+      for (int64_t t = blockIdx.x; t < u.ntiles && !*abort_flag; t += gridDim.x) {
+        if (issued >= kUpdStages && !mbar_wait(&empty[stage], phase ^ 1, abort_flag, err)) break;
+        uint8_t* dst = stages + (size_t)stage * stage_bytes;
+        mbar_expect_tx(&full[stage], tx_bytes);
+        for (int h = 0; h < 2; ++h) {
+          const int row = (int)(t * kUpdRows + h * 64);
+          uint8_t* d = dst + h * half_bytes;
+          if (u.kcp > 0) {
+            tma_load_2d(&mUh, &full[stage], d, row, 0);
+            tma_load_2d(&mUl, &full[stage], d + u.kcp * 128, row, 0);
+          }
+          tma_load_2d(&mA, &full[stage], d + 2 * u.kcp * 128, row, 0);
+        }
+        ++issued;
+        if (++stage == kUpdStages) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+      const int inflight = issued < kUpdStages ? issued : kUpdStages;
+      for (int i = 0; i < inflight; ++i) {
+        if (--stage < 0) {
+          stage = kUpdStages - 1;
+          phase ^= 1;
+        }
+        const long long t0 = clock64();
+        while (!mbar_try_wait(&full[stage], phase) && clock64() - t0 < kWaitCycles) {
+        }
+      }
+      const long long t0 = clock64();
+      while (!mbar_try_wait(t_full, 0) && clock64() - t0 < kWaitCycles) {
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // --------------------------------------------------------- MMA issuer
+      const uint32_t idesc = idesc_bf16(u.N, 1, 0);  // A MN-major (rows contiguous), B K-major
+      bool ok = mbar_wait(t_full, 0, abort_flag, err);
+      tc_fence_after();
+      const uint32_t tbase = smem_u32(tsm);
+      int stage = 0;
+      uint32_t phase = 0;
+      int64_t it = 0;
+      for (int64_t t = blockIdx.x; ok && t < u.ntiles; t += gridDim.x, ++it) {
+        const int buf = (int)(it & 1);
+        const uint32_t use = (uint32_t)((it >> 1) & 1);
+        if (it >= 2 && !mbar_wait(&acc_empty[buf], use ^ 1, abort_flag, err)) break;
+        if (!mbar_wait(&full[stage], phase, abort_flag, err)) break;
+        tc_fence_after();
+        const uint32_t abase = smem_u32(stages + (size_t)stage * stage_bytes);
+        const uint32_t d_tmem = tmem_base + (uint32_t)(buf * 256);
+        for (int k = 0; k < u.np / 16; ++k) {
+          // A: 16 panel columns = two 1024-byte K atoms; LBO = the other 64-row half
+          const uint64_t ad = smem_desc(abase + k * 2048, (uint32_t)half_bytes, 1024);
+          // B: K block k/4, 32-byte step inside the 128-byte swizzle row
+          const uint64_t bd = smem_desc(tbase + (k >> 2) * tb_bytes + (k & 3) * 32, 16, 1024);
+          umma_bf16(d_tmem, ad, bd, idesc, k > 0 ? 1u : 0u);
+        }
+        umma_commit(&empty[stage]);
+        umma_commit(&acc_full[buf]);
+        if (++stage == kUpdStages) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+      umma_commit(mma_done);
+      const long long t0 = clock64();
+      while (!mbar_try_wait(mma_done, 0) && clock64() - t0 < kWaitCycles) {
+      }
+    }
+  } else {
+    // ------------------------------------------------------------- epilogue
+    const int sub = warp & 3;
+    int64_t it = 0;
+    for (int64_t t = blockIdx.x; t < u.ntiles; t += gridDim.x, ++it) {
+      const int buf = (int)(it & 1);
+      const uint32_t use = (uint32_t)((it >> 1) & 1);
+      if (!mbar_wait(&acc_full[buf], use, abort_flag, err)) break;
+      tc_fence_after();
+      const int64_t row = t * kUpdRows + sub * 32 + lane;
+      const uint32_t tl = tmem_base + ((uint32_t)(sub * 32) << 16) + (uint32_t)(buf * 256);
+      for (int j0 = 0; j0 < u.k1p; j0 += 32) {
+        float h[32], m[32], l[32];
+        tmem_ld32(tl + j0, h);
+        tmem_ld32(tl + u.k1p + j0, m);
+        tmem_ld32(tl + 2 * u.k1p + j0, l);
+        if (row < u.M) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const int j = j0 + i;
+            if (j < u.k1) {
+              const float v = (h[i] + m[i]) + l[i];
+              const __nv_bfloat16 vh = __float2bfloat16_rn(v);
+              const __nv_bfloat16 vl = __float2bfloat16_rn(v - __bfloat162float(vh));
+              Uh_new[row + (int64_t)j * u.ldu] = vh;
+              Ul_new[row + (int64_t)j * u.ldu] = vl;
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      if (lane == 0) mbar_arrive(&acc_empty[buf]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem_base, 512);
+}
+
+__global__ void tc_modes_to_f32_kernel(const __nv_bfloat16* __restrict__ Uh,
+                                       const __nv_bfloat16* __restrict__ Ul, int64_t ldu, int64_t M,
+                                       int k, float* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= M * k) return;
+  const int64_t r = e % M, c = e / M;
+  out[r + c * ldu] = __bfloat162float(Uh[r + c * ldu]) + __bfloat162float(Ul[r + c * ldu]);
+}
+
+// ---------------------------------------------------------------- host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// 2-D BF16 tensor map of a column-major matrix (rows x cols, leading dim ld),
+// box = 64 rows x box_cols columns, 128-byte swizzle, zero fill out of bounds.
+bool make_map(CUtensorMap* m, const void* ptr, int64_t rows, int64_t cols, int64_t ld, int box_cols) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || box_cols < 1 || box_cols > 256) return false;
+  if (((uintptr_t)ptr & 15) || ((ld * 2) & 15)) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)cols};
+  const cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  const cuuint32_t box[2] = {64u, (cuuint32_t)box_cols};
+  const cuuint32_t estr[2] = {1u, 1u};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+GramGeom gram_geom(int64_t M, int kc, int B, int num_sms) {
+  GramGeom g;
+  g.M = M;
+  g.kcp = (kc + 7) & ~7;
+  g.Bp = (B + 7) & ~7;
+  g.np = 2 * g.kcp + g.Bp;
+  g.nslab = (int)ceil_div(g.np, kSlab);
+  g.npair = g.nslab * (g.nslab + 1) / 2;
+  // chunks: at least one per SM, at most 8192 rows, multiples of 64 rows
+  int64_t cr = ceil_div(ceil_div(M, num_sms), kRowsStage) * kRowsStage;
+  if (cr > 8192) cr = 8192;
+  if (cr < kRowsStage) cr = kRowsStage;
+  g.chunk_rows = cr;
+  g.nchunk = ceil_div(M, cr);
+  return g;
+}
+
+size_t gram_smem(const GramGeom& g) {
+  return 1024 + (size_t)kGramStages * g.nslab * kSlab * 128 + 256;
+}
+
+}  // namespace
+
+size_t tc_t3_elems(int K, int maxB) {
+  const int k1p = (K + 15) & ~15;
+  const int np = (2 * ((K + 7) & ~7) + ((maxB + 7) & ~7) + 15) & ~15;
+  return (size_t)3 * k1p * (size_t)(ceil_div(np, 64) * 64);
+}
+
+namespace {
+
+}  // namespace
+
+int tc_gram(const __nv_bfloat16* Uh, const __nv_bfloat16* Ul, int64_t ldu, int kc, const void* A,
+            int64_t lda, int B, int dtype, int64_t M, int num_sms, double** partial,
+            int64_t* partial_cap, int* status, cudaStream_t st) {
+  if (dtype != PSVD_BF16) return PSVD_ERR_UNSUPPORTED;
+  GramGeom g = gram_geom(M, kc, B, num_sms);
+  if (g.np > 256 || M > 0x7fffffffll) return PSVD_ERR_SHAPE;
+  CUtensorMap mUh, mUl, mA;
+  if (!make_map(&mA, A, M, B, lda, g.Bp)) return PSVD_ERR_INVALID_ARG;
+  if (kc > 0) {
+    if (!make_map(&mUh, Uh, M, kc, ldu, g.kcp) || !make_map(&mUl, Ul, M, kc, ldu, g.kcp))
+      return PSVD_ERR_INVALID_ARG;
+  } else {
+    mUh = mA;
+    mUl = mA;
+  }
+  // FP32 chunk partials followed by the FP64 chunk sums (all in one buffer)
+  const int64_t per = (int64_t)g.npair * kSlab * kSlab;
+  const int64_t need = (g.nchunk * per + 1) / 2 + per;
+  if (need > *partial_cap) {
+    if (*partial) {
+      if (cudaStreamSynchronize(st) != cudaSuccess) return PSVD_ERR_CUDA;
+      cudaFree(*partial);
+      *partial = nullptr;
+    }
+    if (cudaMalloc((void**)partial, sizeof(double) * need) != cudaSuccess) {
+      cudaGetLastError();
+      *partial_cap = 0;
+      return PSVD_ERR_ALLOC;
+    }
+    *partial_cap = need;
+  }
+  const size_t smem = gram_smem(g);
+  if (cudaFuncSetAttribute(tc_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
+    return PSVD_ERR_CUDA;
+  const int grid = (int)(g.nchunk < num_sms ? g.nchunk : num_sms);
+  tc_gram_kernel<<<grid, 192, smem, st>>>(mUh, mUl, mA, g, reinterpret_cast<float*>(*partial),
+                                          status);
+  return cudaGetLastError() == cudaSuccess ? PSVD_OK : PSVD_ERR_CUDA;
+}
+
+cudaError_t tc_gram_reduce(const double* partial, int64_t M, int kc, int B, int num_sms, double ff,
+                           const double* D, double* G, double* H, int* status, cudaStream_t st) {
+  GramGeom g = gram_geom(M, kc, B, num_sms);
+  const int64_t per = (int64_t)g.npair * kSlab * kSlab;
+  const double* Ssum = partial + (g.nchunk * per + 1) / 2;
+  tc_gram_sum_kernel<<<(unsigned)ceil_div(per, 256), 256, 0, st>>>(
+      reinterpret_cast<const float*>(partial), g.nchunk, g.npair, const_cast<double*>(Ssum));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int n = kc + B;
+  const int64_t tot = (int64_t)n * n;
+  tc_gram_assemble_kernel<<<(unsigned)ceil_div(tot, 256), 256, 0, st>>>(Ssum, g, kc, B, D, ff, G, H,
+                                                                        status);
+  return cudaGetLastError();
+}
+
+int tc_update(const __nv_bfloat16* Uh, const __nv_bfloat16* Ul, int64_t ldu, int kc, const void* A,
+              int64_t lda, int B, int dtype, int64_t M, const float* T, int n, int k1,
+              __nv_bfloat16* T3, __nv_bfloat16* Uh_new, __nv_bfloat16* Ul_new, int num_sms,
+              int* status, cudaStream_t st) {
+  if (dtype != PSVD_BF16) return PSVD_ERR_UNSUPPORTED;
+  UpdGeom u;
+  u.M = M;
+  u.kcp = (kc + 7) & ~7;
+  u.Bp = (B + 7) & ~7;
+  u.np = 2 * u.kcp + u.Bp;
+  u.np = (u.np + 15) & ~15;  // MMA K steps of 16 columns (extra columns read as zero)
+  u.k1 = k1;
+  u.k1p = (k1 + 15) & ~15;
+  u.N = 3 * u.k1p;
+  u.nkb = (int)ceil_div(u.np, 64);
+  u.ntiles = ceil_div(M, kUpdRows);
+  u.ldu = ldu;
+  if (u.np > 256 || u.N > 256 || M > 0x7fffffffll) return PSVD_ERR_SHAPE;
+  const int npk = u.nkb * 64;
+  const int64_t tcount = (int64_t)u.N * npk;
+  tc_pack_T_kernel<<<(unsigned)ceil_div(tcount, 256), 256, 0, st>>>(T, n, kc, u, npk, T3);
+  if (cudaGetLastError() != cudaSuccess) return PSVD_ERR_CUDA;
+  CUtensorMap mUh, mUl, mA, mT;
+  // the A operand spans np (16-padded) columns: the maps deliver zeros past the data
+  if (!make_map(&mA, A, M, B, lda, u.np - 2 * u.kcp)) return PSVD_ERR_INVALID_ARG;
+  if (kc > 0) {
+    if (!make_map(&mUh, Uh, M, kc, ldu, u.kcp) || !make_map(&mUl, Ul, M, kc, ldu, u.kcp))
+      return PSVD_ERR_INVALID_ARG;
+  } else {
+    mUh = mA;
+    mUl = mA;
+  }
+  // T3 is N rows x npk columns, row-major: a "column-major" npk x N matrix
+  if (!make_map(&mT, T3, npk, u.N, npk, u.N)) return PSVD_ERR_INVALID_ARG;
+  const size_t smem = 1024 + (size_t)kUpdStages * 2 * u.np * 128 + (size_t)u.nkb * u.N * 128 + 256;
+  if (smem > 232448) return PSVD_ERR_SHAPE;
+  if (cudaFuncSetAttribute(tc_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
+    return PSVD_ERR_CUDA;
+  const int grid = (int)(u.ntiles < num_sms ? u.ntiles : num_sms);
+  tc_update_kernel<<<grid, 192, smem, st>>>(mUh, mUl, mA, mT, u, Uh_new, Ul_new, status);
+  return cudaGetLastError() == cudaSuccess ? PSVD_OK : PSVD_ERR_CUDA;
+}
+
+cudaError_t tc_modes_to_f32(const __nv_bfloat16* Uh, const __nv_bfloat16* Ul, int64_t ldu,
+                            int64_t M, int k, float* out, cudaStream_t st) {
+  const int64_t tot = M * k;
+  if (tot == 0) return cudaSuccess;
+  tc_modes_to_f32_kernel<<<(unsigned)ceil_div(tot, 256), 256, 0, st>>>(Uh, Ul, ldu, M, k, out);
+  return cudaGetLastError();
 }
 
 }  // namespace psvd

@@ -30,6 +30,7 @@ PSVD_ERR_CUDA = -5
 PSVD_ERR_ALLOC = -6
 PSVD_ERR_IO = -7
 PSVD_ERR_UNSUPPORTED = -8
+PSVD_ERR_TIMEOUT = -9
 
 PSVD_F32, PSVD_BF16, PSVD_F64 = 0, 1, 2
 PSVD_PREC_FP32, PSVD_PREC_BF16_TC = 0, 1

@@ -1,0 +1,78 @@
+"""Parity of the BF16 tensor-core (tcgen05) path with the FP64 oracle, via the C-ABI.
+
+Tolerances for this path (BF16 snapshots, modes held as a BF16 hi/lo pair):
+singular values within 1e-4 relative and the kept subspace within 1e-3 rad,
+widened by the representation floor of the modes (unit 2^-17 instead of u32,
+see test_gpu_fp32).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2108_08845_gb300 import psvd, synthetic
+from tests.test_gpu_fp32 import _batches, _compare, _gpu_run, _oracle_run
+
+pytestmark = pytest.mark.gpu
+
+TC = psvd.PSVD_PREC_BF16_TC
+U17 = 2.0 ** -17
+
+
+def _bf16(bs):
+    return [synthetic.to_storage(b, torch.bfloat16) for b in bs]
+
+
+def test_tc_gram_matches_householder_R():
+    # parallel_qr on a tensor-core handle: R = chol(Gram) from the tcgen05 Gram kernel
+    rng = np.random.default_rng(11)
+    M, n = 9001, 100
+    P = torch.from_numpy(rng.standard_normal((M, n))).to(torch.bfloat16)
+    Pc = P.T.contiguous().T.cuda()
+    h = psvd.psvd_create(M, 16, 100, 1.0, TC)
+    R = torch.zeros((n, n), dtype=torch.float64, device="cuda").T
+    psvd.psvd_parallel_qr(h, Pc, R)
+    psvd.psvd_destroy(h)
+    _, Ro = oracle.householder_qr(P.double().numpy())
+    err = np.abs(R.cpu().numpy() - Ro).max() / np.abs(Ro).max()
+    assert err <= 2e-6, f"R rel err {err:.3e}"
+
+
+def test_tc_config1_bf16():
+    A, _, _, _ = synthetic.low_rank(4096, 100, 40, 1e-8, seed=1234)
+    bs = _bf16(_batches(A, 25))
+    U, D, info = _gpu_run(bs, K=10, ff=1.0, precision=TC)
+    Uo, Do = _oracle_run(bs, 10, 1.0)
+    _compare(U, D, Uo, Do, sig_tol=1e-4, ang_tol=1e-3, unit=U17)
+
+
+@pytest.mark.parametrize("M,K,B,nb,ff", [
+    (5000, 10, 25, 4, 1.0),    # kc, B not multiples of 8; ragged row tiles
+    (3001, 40, 25, 3, 0.95),   # mode count grows from 25 to 40
+    (8192, 16, 48, 4, 0.9),
+])
+def test_tc_low_rank_shapes(M, K, B, nb, ff):
+    s = [10.0 ** (-i / 24.0) for i in range(48)]
+    A, _, _, _ = synthetic.low_rank(M, B * nb, 48, 1e-7, seed=M + K, s=s)
+    bs = _bf16(_batches(A, B))
+    U, D, _ = _gpu_run(bs, K=K, ff=ff, precision=TC)
+    Uo, Do = _oracle_run(bs, K, ff)
+    _compare(U, D, Uo, Do, sig_tol=1e-4, ang_tol=1e-3, unit=U17)
+
+
+def test_tc_travelling_waves_c3_shape():
+    # config-3 recipe (256 modes, amplitudes j^-1.2, noise 1e-4, K=64, B=128,
+    # BF16 snapshots) on a 125 x 256 grid: M = 32000, a ragged last row tile
+    gen = synthetic.TravellingWaves(125, 256, 256, 1.2, 1e-4, seed=1236)
+    bs = _bf16([gen.batch(i, 128) for i in range(3)])
+    U, D, info = _gpu_run(bs, K=64, ff=0.95, precision=TC)
+    Uo, Do = _oracle_run(bs, 64, 0.95)
+    _compare(U, D, Uo, Do, sig_tol=1e-4, ang_tol=1e-3, unit=U17)
+
+
+def test_tc_agrees_with_fp32_path():
+    gen = synthetic.TravellingWaves(64, 128, 64, 1.5, 1e-3, seed=77)
+    bs = _bf16([gen.batch(i, 64) for i in range(3)])
+    Ut, Dt, _ = _gpu_run(bs, K=32, ff=0.95, precision=TC)
+    Uf, Df, _ = _gpu_run(bs, K=32, ff=0.95, precision=psvd.PSVD_PREC_FP32)
+    _compare(Ut, Dt, Uf, Df, sig_tol=1e-4, ang_tol=1e-3, unit=U17)
