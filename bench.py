@@ -37,12 +37,19 @@ METRIC = "snapshots/s at M=2^23,K=64: FP32 plain vs BF16-TC+refine, Ïƒ rel err â
 UNIT = "snapshots/s"
 
 NY, NX, NMODES, DECAY, NOISE, CORR = 2048, 4096, 256, 1.2, 1e-4, 16.0
-M_FULL = NY * NX
+M_FULL = NY * NX  # replaced by --ny/--nx (smaller grids for profiling captures)
 K_MODES, BATCH, FF, SEED = 64, 128, 0.95, 1236
 WORKLOAD = ("M=2^23 (2048x4096 grid), K=64, B=128 BF16 snapshots, ff=0.95, "
             "travelling waves: 256 modes, amplitudes j^-1.2, noise 1e-4")
 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 FMA units x 2 flops x max SM clock
+
+
+def set_grid(ny: int, nx: int):
+    global NY, NX, M_FULL, WORKLOAD
+    NY, NX, M_FULL = ny, nx, ny * nx
+    if (ny, nx) != (2048, 4096):
+        WORKLOAD = WORKLOAD.replace("M=2^23 (2048x4096 grid)", f"M={M_FULL} ({ny}x{nx} grid)")
 
 
 def _dist():
@@ -270,7 +277,10 @@ def main():
     ap.add_argument("--precision", default="both", choices=["both", "fp32", "bf16_tc"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--ny", type=int, default=NY, help="grid rows (profiling on smaller grids)")
+    ap.add_argument("--nx", type=int, default=NX, help="grid columns")
     args = ap.parse_args()
+    set_grid(args.ny, args.nx)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
@@ -310,8 +320,9 @@ def main():
     else:
         ms_max = ms_local
     value = ws * args.steps * BATCH / (ms_max * 1e-3)
-    e2e = run_e2e(psvd, batches, prec_code[head], args.e2e_steps, stream)
-    if ws > 1:
+    e2e = (run_e2e(psvd, batches, prec_code[head], args.e2e_steps, stream) if args.e2e_steps > 0
+           else None)
+    if ws > 1 and e2e:
         t = torch.tensor([e2e["value"]], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MIN)
         e2e["value"] = float(t.item()) * ws

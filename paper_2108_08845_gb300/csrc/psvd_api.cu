@@ -220,7 +220,7 @@ int step(psvd_ctx* h, const void* A, int64_t lda, int B, int dtype) {
   w.Dnew = Dnext;
   pr = prof_begin(h, 1);
   int nl = 0;
-  CK(small_solve_launch(w, n, kc, k1, Dcur, h->cfg.ff, /*refine_steps=*/2, /*max_sweeps=*/12,
+  CK(small_solve_launch(w, n, kc, k1, Dcur, h->cfg.ff, /*refine_steps=*/3, /*max_sweeps=*/12,
                         h->st, &nl));
   prof_end(h, pr);
   h->launches += nl;

@@ -34,6 +34,10 @@ constexpr int JT = 1024;
 constexpr double kLambdaFloor = 1e-9;
 constexpr double kSigmaFloor = 3.1622776601683795e-5;  // sqrt(kLambdaFloor)
 
+// Sort key with a total order: NaN ranks below every number (ties broken by index
+// by the callers), so descending ranks are always a permutation.
+__device__ __forceinline__ double sort_key(double x) { return isnan(x) ? -INFINITY : x; }
+
 __device__ __forceinline__ int pidx(int i, int j) {  // packed upper, i <= j
   return j * (j + 1) / 2 + i;
 }
@@ -54,38 +58,53 @@ __global__ void __launch_bounds__(JT) jacobi_eig_kernel(const double* __restrict
   extern __shared__ __align__(16) float sm[];
   __shared__ float cs_c[kMaxN / 2], cs_s[kMaxN / 2];
   __shared__ int pp[kMaxN / 2], qq[kMaxN / 2];
-  __shared__ int rot_any, rot_round;
+  __shared__ int rot_any, rot_flag[2];
+  __shared__ float dmax;
   __shared__ int rank_of[kMaxN];
   const int N = (n + 1) & ~1;
   const int P = N / 2;
-  const int tid = threadIdx.x;
+  const int LDV = (N + 3) & ~3;  // 16-byte aligned eigenvector columns
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int npk = ((N * (N + 1) / 2) + 3) & ~3;
   float* Hp = sm;        // packed upper triangle of the working matrix
-  float* V = sm + npk;   // N x N eigenvector matrix, column-major
+  float* V = sm + npk;   // N x N eigenvector matrix, column-major, ld LDV
 
   for (int e = tid; e < N * N; e += JT) {
     const int i = e % N, j = e / N;
     if (i <= j) Hp[pidx(i, j)] = (i < n && j < n) ? (float)H[i + (int64_t)j * n] : 0.f;
-    V[e] = (i == j) ? 1.f : 0.f;
+    V[i + j * LDV] = (i == j) ? 1.f : 0.f;
   }
   __syncthreads();
+  if (tid == 0) {
+    float m = 0.f;
+    for (int i = 0; i < n; ++i) m = fmaxf(m, fabsf(Hp[pidx(i, i)]));
+    dmax = m;
+    rot_flag[0] = rot_flag[1] = 0;
+  }
+  __syncthreads();
+  // pairs whose diagonal entries are both below the Gram's resolution carry no
+  // information: they are not rotated (they would keep the sweeps going)
+  const float floor_d = (float)kLambdaFloor * dmax;
 
   int sweep = 0;
+  int gr = 0;  // round counter across sweeps: selects the double-buffered round flag
   bool converged = false;
   while (sweep < max_sweeps) {
     ++sweep;
-    if (tid == 0) rot_any = 0;
-    __syncthreads();
-    for (int r = 0; r < N - 1; ++r) {
-      if (tid == 0) rot_round = 0;
+    if (tid == 0) rot_any = 0;  // every thread read it before the barrier that ended the last sweep
+    for (int r = 0; r < N - 1; ++r, ++gr) {
       __syncthreads();
+      // all threads finished the previous round (and read its flag): clear the
+      // flag the next round will use
+      if (tid == 0) rot_flag[(gr + 1) & 1] = 0;
       // rotation of each disjoint pair (p, q): zeroes H_pq (Golub & Van Loan sym.schur2)
       if (tid < P) {
         int p = tour_player(tid, r, N), q = tour_player(N - 1 - tid, r, N);
         if (p > q) { const int t = p; p = q; q = t; }
         const float app = Hp[pidx(p, p)], aqq = Hp[pidx(q, q)], apq = Hp[pidx(p, q)];
         float c = 1.f, s = 0.f;
-        if (apq != 0.f && fabsf(apq) > tol * sqrtf(fabsf(app)) * sqrtf(fabsf(aqq))) {
+        if (apq != 0.f && (fabsf(app) > floor_d || fabsf(aqq) > floor_d) &&
+            fabsf(apq) > tol * sqrtf(fabsf(app)) * sqrtf(fabsf(aqq))) {
           const float th = (aqq - app) / (2.f * apq);
           const float at = fabsf(th);
           float t = (at > 1e18f) ? 0.5f / at : 1.f / (at + sqrtf(1.f + th * th));
@@ -96,7 +115,7 @@ __global__ void __launch_bounds__(JT) jacobi_eig_kernel(const double* __restrict
           Hp[pidx(q, q)] = aqq + t * apq;
           Hp[pidx(p, q)] = 0.f;
           rot_any = 1;
-          rot_round = 1;
+          rot_flag[gr & 1] = 1;
         }
         pp[tid] = p;
         qq[tid] = q;
@@ -104,53 +123,59 @@ __global__ void __launch_bounds__(JT) jacobi_eig_kernel(const double* __restrict
         cs_s[tid] = s;
       }
       __syncthreads();
-      if (!rot_round) {  // no pair rotated in this round: nothing to apply
-        continue;
+      if (!rot_flag[gr & 1]) continue;  // no pair rotated in this round: nothing to apply
+      // off-diagonal 2x2 blocks B_kl <- J_k^T B_kl J_l, k < l: warp w takes block
+      // rows k = w, w+32, ..., its lanes the columns l > k
+      for (int k = warp; k < P; k += JT / 32) {
+        const float sk = cs_s[k], ck = cs_c[k];
+        const int pk = pp[k], qk = qq[k];
+        for (int l = k + 1 + lane; l < P; l += 32) {
+          const float sl = cs_s[l];
+          if (sk == 0.f && sl == 0.f) continue;
+          const float cl = cs_c[l];
+          const int pl = pp[l], ql = qq[l];
+          const int i11 = pidx_any(pk, pl), i12 = pidx_any(pk, ql), i21 = pidx_any(qk, pl),
+                    i22 = pidx_any(qk, ql);
+          const float x11 = Hp[i11], x12 = Hp[i12], x21 = Hp[i21], x22 = Hp[i22];
+          const float y11 = ck * x11 - sk * x21, y12 = ck * x12 - sk * x22;
+          const float y21 = sk * x11 + ck * x21, y22 = sk * x12 + ck * x22;
+          Hp[i11] = cl * y11 - sl * y12;
+          Hp[i12] = sl * y11 + cl * y12;
+          Hp[i21] = cl * y21 - sl * y22;
+          Hp[i22] = sl * y21 + cl * y22;
+        }
       }
-      // off-diagonal 2x2 blocks: B_kl <- J_k^T B_kl J_l (each entry in one block)
-      for (int e = tid; e < P * P; e += JT) {
-        const int k = e / P, l = e % P;
-        if (k >= l) continue;
-        const float sk = cs_s[k], sl = cs_s[l];
-        if (sk == 0.f && sl == 0.f) continue;
-        const float ck = cs_c[k], cl = cs_c[l];
-        const int pk = pp[k], qk = qq[k], pl = pp[l], ql = qq[l];
-        const int i11 = pidx_any(pk, pl), i12 = pidx_any(pk, ql), i21 = pidx_any(qk, pl),
-                  i22 = pidx_any(qk, ql);
-        const float x11 = Hp[i11], x12 = Hp[i12], x21 = Hp[i21], x22 = Hp[i22];
-        const float y11 = ck * x11 - sk * x21, y12 = ck * x12 - sk * x22;
-        const float y21 = sk * x11 + ck * x21, y22 = sk * x12 + ck * x22;
-        Hp[i11] = cl * y11 - sl * y12;
-        Hp[i12] = sl * y11 + cl * y12;
-        Hp[i21] = cl * y21 - sl * y22;
-        Hp[i22] = sl * y21 + cl * y22;
-      }
-      // eigenvector columns: V <- V J
-      for (int e = tid; e < P * N; e += JT) {
-        const int k = e / N, i = e % N;
+      // eigenvector columns V <- V J, four rows per item
+      const int nq = LDV / 4;
+      for (int e = tid; e < P * nq; e += JT) {
+        const int k = e / nq, c4 = e - k * nq;
         const float s = cs_s[k];
         if (s == 0.f) continue;
         const float c = cs_c[k];
-        float* vp = &V[i + pp[k] * N];
-        float* vq = &V[i + qq[k] * N];
-        const float a = *vp, b = *vq;
-        *vp = c * a - s * b;
-        *vq = s * a + c * b;
+        float4* vp = reinterpret_cast<float4*>(&V[pp[k] * LDV]) + c4;
+        float4* vq = reinterpret_cast<float4*>(&V[qq[k] * LDV]) + c4;
+        const float4 a = *vp, b = *vq;
+        *vp = make_float4(c * a.x - s * b.x, c * a.y - s * b.y, c * a.z - s * b.z, c * a.w - s * b.w);
+        *vq = make_float4(s * a.x + c * b.x, s * a.y + c * b.y, s * a.z + c * b.z, s * a.w + c * b.w);
       }
-      __syncthreads();
     }
-    if (!rot_any) {
+    __syncthreads();
+    const int any = rot_any;
+    __syncthreads();  // every thread has read rot_any before thread 0 resets it
+    if (!any) {
       converged = true;
       break;
     }
   }
+  __syncthreads();
   // sort eigenvalues descending (stable on index) and write FP64 outputs
   if (tid < n) {
     const float li = Hp[pidx(tid, tid)];
+    const double ki = sort_key((double)li);
     int rank = 0;
     for (int j = 0; j < n; ++j) {
-      const float lj = Hp[pidx(j, j)];
-      rank += (lj > li) || (lj == li && j < tid);
+      const double kj = sort_key((double)Hp[pidx(j, j)]);
+      rank += (kj > ki) || (kj == ki && j < tid);
     }
     rank_of[tid] = rank;
     lam[rank] = (double)li;
@@ -158,7 +183,7 @@ __global__ void __launch_bounds__(JT) jacobi_eig_kernel(const double* __restrict
   __syncthreads();
   for (int e = tid; e < n * n; e += JT) {
     const int i = e % n, j = e / n;
-    X[i + (int64_t)rank_of[j] * n] = (double)V[i + j * N];
+    X[i + (int64_t)rank_of[j] * n] = (double)V[i + j * LDV];
   }
   if (tid == 0) {
     info[info_slot] = sweep;
@@ -233,10 +258,13 @@ __global__ void oa_correct_kernel(int n, int nJ, const double* __restrict__ S,
     } else {
       const double lti = (i < nJ) ? S[i + (int64_t)i * n] / XtX[i + (int64_t)i * n] : lam[i];
       const double gap = ltj - lti;
-      if (fabs(gap) > tau * fmax(fabs(ltj), fabs(lti)))
-        e = (Sj[i] + ltj * rr) / gap;
-      else
-        e = 0.5 * rr;
+      e = 0.5 * rr;
+      if (fabs(gap) > tau * fmax(fabs(ltj), fabs(lti))) {
+        // first-order correction; one that is not small means the pair is not
+        // separated at the current accuracy: treat it as a cluster
+        const double f = (Sj[i] + ltj * rr) / gap;
+        if (fabs(f) <= 0.25) e = f;
+      }
     }
     E[i + (int64_t)j * n] = e;
   }
@@ -244,6 +272,30 @@ __global__ void oa_correct_kernel(int n, int nJ, const double* __restrict__ S,
     lamJ[j] = ltj;
     if (!isfinite(ltj)) atomicOr(&info[2], 4);
   }
+}
+
+// lamJ[j] = x_j^T (H x_j) / x_j^T x_j for the refined columns (W = H X_J given).
+__global__ void rayleigh_kernel(int n, int nJ, const double* __restrict__ X,
+                                const double* __restrict__ W, double* __restrict__ lamJ) {
+  __shared__ double s_num[256], s_den[256];
+  const int j = blockIdx.x;
+  double num = 0.0, den = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double x = X[i + (int64_t)j * n];
+    num = fma(x, W[i + (int64_t)j * n], num);
+    den = fma(x, x, den);
+  }
+  s_num[threadIdx.x] = num;
+  s_den[threadIdx.x] = den;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      s_num[threadIdx.x] += s_num[threadIdx.x + o];
+      s_den[threadIdx.x] += s_den[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) lamJ[j] = s_num[0] / s_den[0];
 }
 
 __global__ void copy_cols_kernel(const double* __restrict__ src, double* __restrict__ dst,
@@ -258,14 +310,16 @@ __global__ void finalize_kernel(int n, int nJ, int kc, int k1, const double* __r
                                 double ff, float* __restrict__ T, __nv_bfloat16* __restrict__ T3,
                                 double* __restrict__ Dnew, int* __restrict__ info) {
   __shared__ int order[kMaxN];
-  __shared__ double sig[kMaxN];
+  __shared__ double sig[kMaxN], xn[kMaxN];
   const int tid = threadIdx.x;
+  if (tid < kMaxN) order[tid] = 0;
+  __syncthreads();
   if (tid < nJ) {
-    const double li = lamJ[tid];
+    const double ki = sort_key(lamJ[tid]);
     int rank = 0;
     for (int j = 0; j < nJ; ++j) {
-      const double lj = lamJ[j];
-      rank += (lj > li) || (lj == li && j < tid);
+      const double kj = sort_key(lamJ[j]);
+      rank += (kj > ki) || (kj == ki && j < tid);
     }
     order[rank] = tid;
   }
@@ -274,6 +328,12 @@ __global__ void finalize_kernel(int n, int nJ, int kc, int k1, const double* __r
     const double l = lamJ[order[tid]];
     sig[tid] = (l > 0.0) ? sqrt(l) : 0.0;
     if (!isfinite(l)) atomicOr(&info[2], 4);
+    double x2 = 0.0;
+    for (int i = 0; i < n; ++i) {
+      const double x = X[i + (int64_t)order[tid] * n];
+      x2 = fma(x, x, x2);
+    }
+    xn[tid] = sqrt(x2);
   }
   __syncthreads();
   const double s0 = sig[0];
@@ -292,7 +352,7 @@ __global__ void finalize_kernel(int n, int nJ, int kc, int k1, const double* __r
     const int i = e % n, k = e / n;
     const double s = sig[k];
     const double scale = (i < kc) ? ff * D[i] : 1.0;
-    const double t = (s > 0.0) ? scale * X[i + (int64_t)order[k] * n] / s : 0.0;
+    const double t = (s > 0.0) ? scale * X[i + (int64_t)order[k] * n] / (s * xn[k]) : 0.0;
     T[i + (int64_t)k * n] = (float)t;
     if (T3) {
       // exact triple split t = h + m + l (24 significant bits) for BF16 operands
@@ -351,20 +411,21 @@ cudaError_t dgemm(int m, int nn, int k, double alpha, const double* A, int lda, 
 size_t jacobi_smem_bytes(int n) {
   const int N = (n + 1) & ~1;
   const int npk = ((N * (N + 1) / 2) + 3) & ~3;
-  return sizeof(float) * ((size_t)npk + (size_t)N * N);
+  const int ldv = (N + 3) & ~3;
+  return sizeof(float) * ((size_t)npk + (size_t)N * ldv);
 }
 
 cudaError_t small_solve_launch(const SmallWork& w, int n, int kc, int k1, const double* D,
                                double ff, int refine_steps, int max_sweeps, cudaStream_t st,
                                int* launches) {
-  *launches = 5 + 6 * refine_steps + (refine_steps == 0 ? 1 : 0) + 1;
+  *launches = 5 + 6 * refine_steps + 2 + 1;
   const size_t smem = jacobi_smem_bytes(n);
   cudaError_t e = cudaFuncSetAttribute(jacobi_eig_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   // stage 1: FP32 Jacobi on H -> X1 (in E), eigenvalues (in lamJ, unused)
-  // stage 1 stalls at the FP32 rounding floor after a handful of sweeps
-  const int stage1_sweeps = (max_sweeps < 5) ? max_sweeps : 5;
+  // stage 1 only has to reach the FP32 rounding floor; stage 2 does the rest
+  const int stage1_sweeps = (max_sweeps < 3) ? max_sweeps : 3;
   jacobi_eig_kernel<<<1, JT, smem, st>>>(w.H, n, w.E, w.lamJ, stage1_sweeps, 2e-6f, w.info, 0, 0);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // stage 2: H2 = X1^T H X1 (FP64, in S), FP32 Jacobi on H2 -> X2 (in R), lam
@@ -390,11 +451,11 @@ cudaError_t small_solve_launch(const SmallWork& w, int n, int kc, int k1, const 
     copy_cols_kernel<<<(unsigned)ceil_div(cnt, 256), 256, 0, st>>>(w.Xn, w.X, cnt);
     if ((e = cudaGetLastError())) return e;
   }
-  if (refine_steps == 0) {
-    const int64_t cnt = nJ;
-    copy_cols_kernel<<<(unsigned)ceil_div(cnt, 256), 256, 0, st>>>(w.lam, w.lamJ, cnt);
-    if ((e = cudaGetLastError())) return e;
-  }
+  // eigenvalues consistent with the final vectors: sigma_j^2 = x_j^T H x_j / x_j^T x_j,
+  // so that every new mode P x_j / sigma_j has unit norm
+  if ((e = dgemm<false>(n, nJ, n, 1.0, w.H, n, w.X, n, 0.0, nullptr, n, w.W, n, st))) return e;
+  rayleigh_kernel<<<nJ, 256, 0, st>>>(n, nJ, w.X, w.W, w.lamJ);
+  if ((e = cudaGetLastError())) return e;
   finalize_kernel<<<1, 256, 0, st>>>(n, nJ, kc, k1, w.X, w.lamJ, D, ff, w.T, nullptr, w.Dnew, w.info);
   return cudaGetLastError();
 }

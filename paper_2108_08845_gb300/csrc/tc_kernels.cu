@@ -9,11 +9,12 @@
 //
 // tc_gram_kernel: the panel Gram P'^T P' (step 1's R^T R).  P' is streamed in
 //   64-row stages by TMA (SWIZZLE_128B, each column one 128-byte row, i.e. the
-//   K-major canonical layout with K = rows); for every pair of 128-column slabs
-//   (i <= j) one tcgen05.mma per 16 rows accumulates slab_i^T slab_j into TMEM.
-//   A row chunk's accumulators are drained by four epilogue warps to FP32
-//   partials in global memory, summed in FP64 in a fixed order by
-//   tc_gram_reduce_kernel, which also folds Uh/Ul back into U.
+//   K-major canonical layout with K = rows).  Each CTA owns one pair of
+//   128-column slabs (i <= j) over one row range and issues one tcgen05.mma per
+//   16 rows into an FP32 TMEM accumulator; every 128 rows the epilogue folds
+//   that accumulator into a float-float (hi, lo) sum held in TMEM (TwoSum), so
+//   FP32 rounding only acts on 8-MMA chains.  The range blocks are summed in
+//   FP64 in a fixed order and Uh/Ul are folded back into U on the small side.
 // tc_update_kernel: step 4, U_new = [U | A] T.  T (n x k1, FP32) is split
 //   exactly into three BF16 parts, so one MMA with N = 3 * k1p computes the
 //   three partial products; P' row tiles of 128 rows are the MN-major A operand
@@ -28,6 +29,7 @@
 // waits (bounded) for its own copies and frees its TMEM before returning.
 #include <cuda.h>
 #include <stdio.h>
+#include <stdlib.h>
 
 #include "tc_kernels.cuh"
 
@@ -126,6 +128,25 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
           smem_u32(bar))
       : "memory");
 }
+// 32 consecutive TMEM columns of this thread's lane, without waiting.
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
 // 32 consecutive TMEM columns of this thread's lane.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   uint32_t r[32];
@@ -142,6 +163,35 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Stores 32 consecutive TMEM columns of this thread's lane (no wait).
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+      "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+      "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+      "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])),
+      "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])),
+      "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])),
+      "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])),
+      "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])),
+      "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+      : "memory");
+}
+
+// Knuth TwoSum: hi + lo accumulates x with the rounding error of hi + x kept in lo.
+__device__ __forceinline__ void two_sum_fold(float& hi, float& lo, float x) {
+  const float s = __fadd_rn(hi, x);
+  const float bp = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+  hi = s;
+  lo = __fadd_rn(lo, err);
 }
 
 // Shared-memory matrix descriptor, SWIZZLE_128B (layout type 2), version 1.
@@ -175,8 +225,15 @@ struct GramGeom {
   int np;      // 2*kcp + Bp
   int nslab;   // ceil(np / 128)
   int npair;   // nslab*(nslab+1)/2
-  int64_t chunk_rows;  // rows per accumulation chunk (multiple of 64)
-  int64_t nchunk;
+  int64_t range_rows;  // rows per CTA range (multiple of 64)
+  int64_t nrange;
+  int fold_stages;     // 64-row stages (4 MMAs each) per FP32 accumulation chain
+};
+
+// Tensor maps of the three panel planes (Uh, Ul, A) with boxes of 64 rows x
+// {64, 32, 16, 8} columns, so that any 8-aligned column range is tiled exactly.
+struct PanelMaps {
+  CUtensorMap m[3][4];
 };
 
 __device__ __forceinline__ void pair_of(int p, int nslab, int* i, int* j) {
@@ -194,30 +251,60 @@ __device__ __forceinline__ int slab_width16(int s, int np) {
   return (w + 15) & ~15;
 }
 
-// partial layout: [chunk][pair][128 lanes][128 columns] FP32
-__global__ void __launch_bounds__(192, 1) tc_gram_kernel(const __grid_constant__ CUtensorMap mUh,
-                                                         const __grid_constant__ CUtensorMap mUl,
-                                                         const __grid_constant__ CUtensorMap mA,
-                                                         GramGeom g, float* __restrict__ partial,
+// Loads slab s (padded-panel columns [128 s, 128 s + 128)) for rows [row, row + 64)
+// into dst: each plane's column range inside the slab is tiled by boxes of 64,
+// 32, 16 and 8 columns.
+__device__ __forceinline__ void load_slab(const PanelMaps& pm, const GramGeom& g, int s,
+                                          uint64_t* bar, uint8_t* dst, int row) {
+  const int lo = s * kSlab, hi = min(g.np, (s + 1) * kSlab);
+  const int start[3] = {0, g.kcp, 2 * g.kcp};
+  const int end[3] = {g.kcp, 2 * g.kcp, g.np};
+  for (int src = 0; src < 3; ++src) {
+    int c = max(lo, start[src]);
+    const int c_end = min(hi, end[src]);
+    while (c < c_end) {
+      const int left = c_end - c;
+      const int wi = left >= 64 ? 0 : left >= 32 ? 1 : left >= 16 ? 2 : 3;
+      tma_load_2d(&pm.m[src][wi], bar, dst + (c - lo) * 128, row, c - start[src]);
+      c += 64 >> wi;
+    }
+  }
+}
+
+// One CTA = one 128 x 128 block (slab pair) of the Gram over one row range.
+// TMEM: two FP32 accumulators (columns 0 and 128) alternate between the MMA warp
+// and the epilogue, which folds each finished 128-row partial into a float-float
+// running sum (hi at column 256, lo at 384).  The range's block is written as
+// FP64 (hi + lo) to partial[range][pair][128][128].
+__global__ void __launch_bounds__(192, 1) tc_gram_kernel(const __grid_constant__ PanelMaps pm,
+                                                         GramGeom g, double* __restrict__ partial,
                                                          int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  // 1024-byte aligned stage buffers (SWIZZLE_128B atoms)
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const int stage_bytes = g.nslab * kSlab * 128;
+  const int pair = blockIdx.x % g.npair;
+  const int64_t range = blockIdx.x / g.npair;
+  int si, sj;
+  pair_of(pair, g.nslab, &si, &sj);
+  const bool diag = (si == sj);
+  const int nsl = diag ? 1 : 2;
+  const int stage_bytes = nsl * kSlab * 128;
   uint8_t* stages = base;
   uint64_t* full = (uint64_t*)(stages + (size_t)kGramStages * stage_bytes);
   uint64_t* empty = full + kGramStages;
-  uint64_t* acc_full = empty + kGramStages;
-  uint64_t* acc_empty = acc_full + 1;
-  uint64_t* mma_done = acc_empty + 1;
+  uint64_t* acc_full = empty + kGramStages;  // [2]
+  uint64_t* acc_empty = acc_full + 2;        // [2]
+  uint64_t* mma_done = acc_empty + 2;
   uint32_t* tmem_slot = (uint32_t*)(mma_done + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ktiles = (int)(g.chunk_rows / kRowsStage);
-  const uint32_t tx_bytes = (uint32_t)(2 * g.kcp + g.Bp) * 128u;
+  const int64_t r0 = range * g.range_rows;
+  const int64_t r1 = min(g.M, r0 + g.range_rows);
+  const int nst = (r0 < r1) ? (int)ceil_div(r1 - r0, kRowsStage) : 0;
+  const int nfold = (int)ceil_div(nst, g.fold_stages);
+  const int w = slab_width16(sj, g.np);
 
-  // zero the stage buffers once: columns beyond np inside the last slab stay zero
+  // zero the stage buffers once: columns beyond np inside a slab stay zero
   for (int i = threadIdx.x; i < kGramStages * stage_bytes / 16; i += blockDim.x)
     reinterpret_cast<int4*>(stages)[i] = make_int4(0, 0, 0, 0);
   if (threadIdx.x == 0) {
@@ -225,8 +312,10 @@ __global__ void __launch_bounds__(192, 1) tc_gram_kernel(const __grid_constant__
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(acc_full, 1);
-    mbar_init(acc_empty, 4);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);
+    }
     mbar_init(mma_done, 1);
     *abort_flag = 0;
     fence_barrier_init();
@@ -244,30 +333,24 @@ __global__ void __launch_bounds__(192, 1) tc_gram_kernel(const __grid_constant__
   if (warp == 0) {
     if (lane == 0) {
       // ---------------------------------------------------------- TMA producer
-      int stage = 0;
+      int stage = 0, issued = 0;
       uint32_t phase = 0;
-      int issued = 0;
-      for (int64_t c = blockIdx.x; c < g.nchunk && !*abort_flag; c += gridDim.x) {
-        for (int kt = 0; kt < ktiles; ++kt) {
-          const int64_t row = c * g.chunk_rows + (int64_t)kt * kRowsStage;
-          if (row >= g.M) break;
-          if (issued >= kGramStages && !mbar_wait(&empty[stage], phase ^ 1, abort_flag, err)) break;
-          uint8_t* dst = stages + (size_t)stage * stage_bytes;
-          mbar_expect_tx(&full[stage], tx_bytes);
-          if (g.kcp > 0) {
-            tma_load_2d(&mUh, &full[stage], dst, (int)row, 0);
-            tma_load_2d(&mUl, &full[stage], dst + g.kcp * 128, (int)row, 0);
-          }
-          tma_load_2d(&mA, &full[stage], dst + 2 * g.kcp * 128, (int)row, 0);
-          ++issued;
-          if (++stage == kGramStages) {
-            stage = 0;
-            phase ^= 1;
-          }
+      for (int st = 0; st < nst && !*abort_flag; ++st) {
+        if (issued >= kGramStages && !mbar_wait(&empty[stage], phase ^ 1, abort_flag, err)) break;
+        uint8_t* dst = stages + (size_t)stage * stage_bytes;
+        const int row = (int)(r0 + (int64_t)st * kRowsStage);
+        // expected bytes: every 8-column group of the two slabs
+        const uint32_t bytes_i = (uint32_t)(min(g.np, (si + 1) * kSlab) - si * kSlab) * 128u;
+        const uint32_t bytes_j = diag ? 0u : (uint32_t)(min(g.np, (sj + 1) * kSlab) - sj * kSlab) * 128u;
+        mbar_expect_tx(&full[stage], bytes_i + bytes_j);
+        load_slab(pm, g, si, &full[stage], dst, row);
+        if (!diag) load_slab(pm, g, sj, &full[stage], dst + kSlab * 128, row);
+        ++issued;
+        if (++stage == kGramStages) {
+          stage = 0;
+          phase ^= 1;
         }
-        if (*abort_flag) break;
       }
-      // drain: wait (bounded) until the in-flight copies have landed
       const int inflight = issued < kGramStages ? issued : kGramStages;
       for (int i = 0; i < inflight; ++i) {
         if (--stage < 0) {
@@ -282,48 +365,40 @@ __global__ void __launch_bounds__(192, 1) tc_gram_kernel(const __grid_constant__
   } else if (warp == 1) {
     if (lane == 0) {
       // --------------------------------------------------------- MMA issuer
+      const uint32_t idesc = idesc_bf16(w, 0, 0);
       int stage = 0;
       uint32_t phase = 0;
-      uint32_t acc_phase = 0;
-      bool first_chunk = true;
-      for (int64_t c = blockIdx.x; c < g.nchunk; c += gridDim.x) {
-        if (!first_chunk && !mbar_wait(acc_empty, acc_phase ^ 1, abort_flag, err)) break;
-        first_chunk = false;
+      int st = 0;
+      for (int f = 0; f < nfold; ++f) {
+        const int b = f & 1;
+        const uint32_t use = (uint32_t)((f >> 1) & 1);
+        if (f >= 2 && !mbar_wait(&acc_empty[b], use ^ 1, abort_flag, err)) break;
+        const uint32_t d_tmem = tmem_base + (uint32_t)(b * kSlab);
         bool ok = true;
-        int kt = 0;
-        for (; kt < ktiles; ++kt) {
-          const int64_t row = c * g.chunk_rows + (int64_t)kt * kRowsStage;
-          if (row >= g.M) break;
+        for (int k4 = 0; k4 < g.fold_stages && st < nst; ++k4, ++st) {
           if (!mbar_wait(&full[stage], phase, abort_flag, err)) {
             ok = false;
             break;
           }
           tc_fence_after();
           const uint32_t sbase = smem_u32(stages + (size_t)stage * stage_bytes);
-#pragma unroll 1
-          for (int p = 0; p < g.npair; ++p) {
-            int si, sj;
-            pair_of(p, g.nslab, &si, &sj);
-            const uint32_t idesc = idesc_bf16(slab_width16(sj, g.np), 0, 0);
-            const uint32_t d_tmem = tmem_base + (uint32_t)(p * kSlab);
+          const uint32_t abase = sbase;
+          const uint32_t bbase = diag ? sbase : sbase + kSlab * 128;
 #pragma unroll
-            for (int k = 0; k < kRowsStage / 16; ++k) {
-              const uint64_t ad = smem_desc(sbase + si * kSlab * 128 + k * 32, 16, 1024);
-              const uint64_t bd = smem_desc(sbase + sj * kSlab * 128 + k * 32, 16, 1024);
-              umma_bf16(d_tmem, ad, bd, idesc, (kt > 0 || k > 0) ? 1u : 0u);
-            }
+          for (int k = 0; k < kRowsStage / 16; ++k) {
+            const uint64_t ad = smem_desc(abase + k * 32, 16, 1024);
+            const uint64_t bd = smem_desc(bbase + k * 32, 16, 1024);
+            umma_bf16(d_tmem, ad, bd, idesc, (k4 > 0 || k > 0) ? 1u : 0u);
           }
-          umma_commit(&empty[stage]);  // frees the stage when these MMAs complete
+          umma_commit(&empty[stage]);
           if (++stage == kGramStages) {
             stage = 0;
             phase ^= 1;
           }
         }
         if (!ok) break;
-        umma_commit(acc_full);  // chunk accumulated
-        acc_phase ^= 1;
+        umma_commit(&acc_full[b]);
       }
-      // every issued MMA has completed before TMEM is released
       umma_commit(mma_done);
       const long long t0 = clock64();
       while (!mbar_try_wait(mma_done, 0) && clock64() - t0 < kWaitCycles) {
@@ -331,29 +406,58 @@ __global__ void __launch_bounds__(192, 1) tc_gram_kernel(const __grid_constant__
     }
   } else {
     // ------------------------------------------------------------- epilogue
-    const int sub = warp & 3;  // TMEM sub-partition of this warp
-    const int row_in_slab = sub * 32 + lane;
-    uint32_t acc_phase = 0;
-    for (int64_t c = blockIdx.x; c < g.nchunk; c += gridDim.x) {
-      if (!mbar_wait(acc_full, acc_phase, abort_flag, err)) break;
-      acc_phase ^= 1;
-      tc_fence_after();
-      float* out = partial + (size_t)c * g.npair * kSlab * kSlab;
-      for (int p = 0; p < g.npair; ++p) {
-        int si, sj;
-        pair_of(p, g.nslab, &si, &sj);
-        const int w = slab_width16(sj, g.np);
-        float* orow = out + ((size_t)p * kSlab + row_in_slab) * kSlab;
-        for (int c0 = 0; c0 < w; c0 += 32) {
-          float v[32];
-          tmem_ld32(tmem_base + ((uint32_t)(sub * 32) << 16) + (uint32_t)(p * kSlab + c0), v);
-#pragma unroll
-          for (int i = 0; i < 32; i += 4)
-            if (c0 + i < w) *reinterpret_cast<float4*>(&orow[c0 + i]) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-        }
+    const int sub = warp & 3;
+    const uint32_t lane_base = tmem_base + ((uint32_t)(sub * 32) << 16);
+    const uint32_t t_hi = lane_base + 2 * kSlab, t_lo = lane_base + 3 * kSlab;
+    bool ok = true;
+    for (int f = 0; f < nfold; ++f) {
+      const int b = f & 1;
+      const uint32_t use = (uint32_t)((f >> 1) & 1);
+      if (!mbar_wait(&acc_full[b], use, abort_flag, err)) {
+        ok = false;
+        break;
       }
+      tc_fence_after();
+      for (int c0 = 0; c0 < w; c0 += 32) {
+        uint32_t a[32], h[32], l[32];
+        tmem_ld32_nowait(lane_base + (uint32_t)(b * kSlab + c0), a);
+        if (f > 0) {
+          tmem_ld32_nowait(t_hi + c0, h);
+          tmem_ld32_nowait(t_lo + c0, l);
+        }
+        tmem_wait_ld();
+        float fh[32], fl[32];
+        if (f == 0) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            fh[i] = __uint_as_float(a[i]);
+            fl[i] = 0.f;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            fh[i] = __uint_as_float(h[i]);
+            fl[i] = __uint_as_float(l[i]);
+            two_sum_fold(fh[i], fl[i], __uint_as_float(a[i]));
+          }
+        }
+        tmem_st32(t_hi + c0, fh);
+        tmem_st32(t_lo + c0, fl);
+      }
+      tmem_wait_st();
       tc_fence_before();
-      if (lane == 0) mbar_arrive(acc_empty);
+      if (lane == 0) mbar_arrive(&acc_empty[b]);
+    }
+    if (ok && nfold > 0) {
+      const int row_in_slab = sub * 32 + lane;
+      double* orow = partial + (((size_t)range * g.npair + pair) * kSlab + row_in_slab) * kSlab;
+      for (int c0 = 0; c0 < w; c0 += 32) {
+        float h[32], l[32];
+        tmem_ld32(t_hi + c0, h);
+        tmem_ld32(t_lo + c0, l);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) orow[c0 + i] = (double)h[i] + (double)l[i];
+      }
     }
   }
   tc_fence_before();
@@ -362,14 +466,14 @@ __global__ void __launch_bounds__(192, 1) tc_gram_kernel(const __grid_constant__
   if (warp == 1) tmem_dealloc(tmem_base, 512);
 }
 
-// Ssum[pair][x][y] = sum over chunks of the FP32 partials, in FP64, chunk order fixed.
-__global__ void tc_gram_sum_kernel(const float* __restrict__ partial, int64_t nchunk, int npair,
+// Ssum[pair][x][y] = sum over row ranges of the FP64 range blocks, in a fixed order.
+__global__ void tc_gram_sum_kernel(const double* __restrict__ partial, int64_t nrange, int npair,
                                    double* __restrict__ Ssum) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t per = (int64_t)npair * kSlab * kSlab;
   if (e >= per) return;
   double s = 0.0;
-  for (int64_t c = 0; c < nchunk; ++c) s += (double)partial[c * per + e];
+  for (int64_t r = 0; r < nrange; ++r) s += partial[r * per + e];
   Ssum[e] = s;
 }
 
@@ -661,17 +765,21 @@ GramGeom gram_geom(int64_t M, int kc, int B, int num_sms) {
   g.np = 2 * g.kcp + g.Bp;
   g.nslab = (int)ceil_div(g.np, kSlab);
   g.npair = g.nslab * (g.nslab + 1) / 2;
-  // chunks: at least one per SM, at most 8192 rows, multiples of 64 rows
-  int64_t cr = ceil_div(ceil_div(M, num_sms), kRowsStage) * kRowsStage;
-  if (cr > 8192) cr = 8192;
-  if (cr < kRowsStage) cr = kRowsStage;
-  g.chunk_rows = cr;
-  g.nchunk = ceil_div(M, cr);
+  // about one CTA per SM: num_sms / npair row ranges, each a multiple of 64 rows
+  int64_t want = num_sms / g.npair;
+  if (want < 1) want = 1;
+  int64_t rr = ceil_div(ceil_div(M, want), kRowsStage) * kRowsStage;
+  if (rr < kRowsStage) rr = kRowsStage;
+  g.range_rows = rr;
+  g.nrange = ceil_div(M, rr);
+  const char* fs = getenv("PSVD_TC_FOLD_STAGES");  // experiment hook
+  g.fold_stages = fs ? atoi(fs) : 4;
+  if (g.fold_stages < 1) g.fold_stages = 1;
   return g;
 }
 
-size_t gram_smem(const GramGeom& g) {
-  return 1024 + (size_t)kGramStages * g.nslab * kSlab * 128 + 256;
+size_t gram_smem(const GramGeom&) {
+  return 1024 + (size_t)kGramStages * 2 * kSlab * 128 + 256;
 }
 
 }  // namespace
@@ -692,18 +800,21 @@ int tc_gram(const __nv_bfloat16* Uh, const __nv_bfloat16* Ul, int64_t ldu, int k
   if (dtype != PSVD_BF16) return PSVD_ERR_UNSUPPORTED;
   GramGeom g = gram_geom(M, kc, B, num_sms);
   if (g.np > 256 || M > 0x7fffffffll) return PSVD_ERR_SHAPE;
-  CUtensorMap mUh, mUl, mA;
-  if (!make_map(&mA, A, M, B, lda, g.Bp)) return PSVD_ERR_INVALID_ARG;
-  if (kc > 0) {
-    if (!make_map(&mUh, Uh, M, kc, ldu, g.kcp) || !make_map(&mUl, Ul, M, kc, ldu, g.kcp))
-      return PSVD_ERR_INVALID_ARG;
-  } else {
-    mUh = mA;
-    mUl = mA;
+  PanelMaps pm;
+  for (int wi = 0; wi < 4; ++wi) {
+    const int bw = 64 >> wi;
+    if (!make_map(&pm.m[2][wi], A, M, B, lda, bw)) return PSVD_ERR_INVALID_ARG;
+    if (kc > 0) {
+      if (!make_map(&pm.m[0][wi], Uh, M, kc, ldu, bw) || !make_map(&pm.m[1][wi], Ul, M, kc, ldu, bw))
+        return PSVD_ERR_INVALID_ARG;
+    } else {
+      pm.m[0][wi] = pm.m[2][wi];
+      pm.m[1][wi] = pm.m[2][wi];
+    }
   }
-  // FP32 chunk partials followed by the FP64 chunk sums (all in one buffer)
+  // FP64 range blocks followed by their sums (one buffer)
   const int64_t per = (int64_t)g.npair * kSlab * kSlab;
-  const int64_t need = (g.nchunk * per + 1) / 2 + per;
+  const int64_t need = g.nrange * per + per;
   if (need > *partial_cap) {
     if (*partial) {
       if (cudaStreamSynchronize(st) != cudaSuccess) return PSVD_ERR_CUDA;
@@ -717,12 +828,14 @@ int tc_gram(const __nv_bfloat16* Uh, const __nv_bfloat16* Ul, int64_t ldu, int k
     }
     *partial_cap = need;
   }
+  // columns of a block beyond the slab width are never written: keep them zero
+  if (cudaMemsetAsync(*partial, 0, sizeof(double) * g.nrange * per, st) != cudaSuccess)
+    return PSVD_ERR_CUDA;
   const size_t smem = gram_smem(g);
   if (cudaFuncSetAttribute(tc_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
     return PSVD_ERR_CUDA;
-  const int grid = (int)(g.nchunk < num_sms ? g.nchunk : num_sms);
-  tc_gram_kernel<<<grid, 192, smem, st>>>(mUh, mUl, mA, g, reinterpret_cast<float*>(*partial),
-                                          status);
+  const int grid = (int)(g.nrange * g.npair);
+  tc_gram_kernel<<<grid, 192, smem, st>>>(pm, g, *partial, status);
   return cudaGetLastError() == cudaSuccess ? PSVD_OK : PSVD_ERR_CUDA;
 }
 
@@ -730,9 +843,8 @@ cudaError_t tc_gram_reduce(const double* partial, int64_t M, int kc, int B, int 
                            const double* D, double* G, double* H, int* status, cudaStream_t st) {
   GramGeom g = gram_geom(M, kc, B, num_sms);
   const int64_t per = (int64_t)g.npair * kSlab * kSlab;
-  const double* Ssum = partial + (g.nchunk * per + 1) / 2;
-  tc_gram_sum_kernel<<<(unsigned)ceil_div(per, 256), 256, 0, st>>>(
-      reinterpret_cast<const float*>(partial), g.nchunk, g.npair, const_cast<double*>(Ssum));
+  double* Ssum = const_cast<double*>(partial) + g.nrange * per;
+  tc_gram_sum_kernel<<<(unsigned)ceil_div(per, 256), 256, 0, st>>>(partial, g.nrange, g.npair, Ssum);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int n = kc + B;
