@@ -54,7 +54,9 @@ __global__ void __launch_bounds__(JT) jacobi_eig_kernel(const double* __restrict
                                                         double* __restrict__ X,
                                                         double* __restrict__ lam, int max_sweeps,
                                                         float tol, int* __restrict__ info,
-                                                        int info_slot, int flag_unconverged) {
+                                                        int info_slot, int flag_unconverged,
+                                                        const double* __restrict__ ref_lam,
+                                                        int ref_idx, double ref_frac) {
   extern __shared__ __align__(16) float sm[];
   __shared__ float cs_c[kMaxN / 2], cs_s[kMaxN / 2];
   __shared__ int pp[kMaxN / 2], qq[kMaxN / 2];
@@ -82,9 +84,13 @@ __global__ void __launch_bounds__(JT) jacobi_eig_kernel(const double* __restrict
     rot_flag[0] = rot_flag[1] = 0;
   }
   __syncthreads();
-  // pairs whose diagonal entries are both below the Gram's resolution carry no
-  // information: they are not rotated (they would keep the sweeps going)
-  const float floor_d = (float)kLambdaFloor * dmax;
+  // Pairs whose diagonal entries are both below floor_d are not rotated: below
+  // the Gram's resolution (kLambdaFloor * lambda_max) they carry no information,
+  // and with ref_lam (eigenvalue estimates from a previous stage) directions far
+  // below the ref_idx-th eigenvalue need not be separated from each other (the
+  // refinement only needs them as an orthonormal complement of the kept modes).
+  float floor_d = (float)kLambdaFloor * dmax;
+  if (ref_lam) floor_d = fmaxf(floor_d, (float)(ref_frac * ref_lam[ref_idx]));
 
   int sweep = 0;
   int gr = 0;  // round counter across sweeps: selects the double-buffered round flag
@@ -426,14 +432,17 @@ cudaError_t small_solve_launch(const SmallWork& w, int n, int kc, int k1, const 
   // stage 1: FP32 Jacobi on H -> X1 (in E), eigenvalues (in lamJ, unused)
   // stage 1 only has to reach the FP32 rounding floor; stage 2 does the rest
   const int stage1_sweeps = (max_sweeps < 3) ? max_sweeps : 3;
-  jacobi_eig_kernel<<<1, JT, smem, st>>>(w.H, n, w.E, w.lamJ, stage1_sweeps, 2e-6f, w.info, 0, 0);
+  jacobi_eig_kernel<<<1, JT, smem, st>>>(w.H, n, w.E, w.lamJ, stage1_sweeps, 2e-6f, w.info, 0, 0,
+                                          nullptr, 0, 0.0);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // stage 2: H2 = X1^T H X1 (FP64, in S), FP32 Jacobi on H2 -> X2 (in R), lam
   if ((e = dgemm<false>(n, n, n, 1.0, w.H, n, w.E, n, 0.0, nullptr, n, w.W, n, st))) return e;
   if ((e = dgemm<true>(n, n, n, 1.0, w.E, n, w.W, n, 0.0, nullptr, n, w.S, n, st))) return e;
   // stage 2 stops at relative off-diagonals of 1e-4: the FP64 refinement that
   // follows is quadratically convergent from there
-  jacobi_eig_kernel<<<1, JT, smem, st>>>(w.S, n, w.R, w.lam, max_sweeps, 1e-4f, w.info, 1, 1);
+  const int nJ0 = (k1 + kRefineMargin < n) ? k1 + kRefineMargin : n;
+  jacobi_eig_kernel<<<1, JT, smem, st>>>(w.S, n, w.R, w.lam, max_sweeps, 1e-4f, w.info, 1, 1,
+                                          w.lamJ, nJ0 - 1, 1e-2);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // X = X1 X2
   if ((e = dgemm<false>(n, n, n, 1.0, w.E, n, w.R, n, 0.0, nullptr, n, w.X, n, st))) return e;
