@@ -137,6 +137,29 @@ int psvd_parallel_svd(psvd_handle h, const void* A, int64_t lda, const int64_t* 
                       int32_t nparts, int32_t N, int32_t dtype, int32_t r1, int32_t r2,
                       float* U_out, int64_t ldu, double* L_out);
 
+/* psvd_parallel_qr_static: the same R factor as psvd_parallel_qr, computed
+ * without allocating anything (the paper has no counterpart: this serves
+ * callers that cannot allocate device memory when they need the factor, e.g.
+ * a process whose device memory is reserved by another allocator, or a
+ * latency-critical loop where cudaMalloc's implicit device synchronisation
+ * would stall other streams).  No handle is needed.
+ *   P      device pointer to the panel, M x n column-major, ldp >= M, dtype
+ *          PSVD_F32 or PSVD_BF16 (host pointers are rejected: there is no
+ *          staging buffer to copy them into)
+ *   R_out  n x n FP64, leading dimension n, upper triangular with diag >= 0
+ *          (host or device); stream: cudaStream_t, NULL = default stream
+ * Limits: n <= 128 and M >= n, else PSVD_ERR_SHAPE.  Scratch: a 3.4 MB
+ * file-scope device array (the Gram's row-chunk partials, the Gram and a
+ * status word) that every GPU loading the library holds until the process
+ * exits.  The first call on a device looks up the array's device address
+ * (once per device); make that first call before any stream capture.  All
+ * calls share the one array and every call overwrites it, so calls whose work
+ * overlaps on the GPU (different streams or host threads) race: serialise
+ * them.  The call synchronises `stream` before returning.  Returns
+ * PSVD_ERR_NONFINITE if the Gram is not positive definite. */
+int psvd_parallel_qr_static(const void* P, int64_t ldp, int64_t M, int32_t n, int32_t dtype,
+                            double* R_out, void* stream);
+
 /* psvd_get_modes: copies the current modes (M x k, FP32; a BF16 hi/lo pair is
  * summed exactly) into U_out (ldu >= M, host or device). */
 int psvd_get_modes(psvd_handle h, float* U_out, int64_t ldu);

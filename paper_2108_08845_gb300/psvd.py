@@ -90,6 +90,7 @@ def load(build_if_missing: bool = True):
         lib.psvd_status_string.argtypes = [C.c_int]
         lib.psvd_status_string.restype = C.c_char_p
         lib.psvd_last_info.argtypes = [vp, C.POINTER(C.c_int32)]
+        lib.psvd_parallel_qr_static.argtypes = [vp, i64, i64, i32, i32, vp, vp]
         lib.psvd_set_profiling.argtypes = [vp, i32]
         lib.psvd_get_profile.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                          C.POINTER(C.c_int64)]
@@ -186,6 +187,18 @@ def psvd_parallel_qr(h: int, P, R_out) -> int:
     if rcode != PSVD_F64 or rr != n or rc_ != n:
         raise ValueError("R_out: must be an n x n float64 matrix")
     return _check(load().psvd_parallel_qr(h, p, ld, n, code, r), "psvd_parallel_qr")
+
+
+def psvd_parallel_qr_static(P, R_out, stream=None) -> int:
+    """R of psvd_parallel_qr without any allocation (see include/psvd.h): for callers
+    that cannot allocate device memory when they need the factor.  P must be a
+    device matrix with at most 128 columns; calls that overlap on the GPU race."""
+    p, ld, M, n, code, _keep = _mat(P, "P")
+    r, _, rr, rc_, rcode, _keep2 = _mat(R_out, "R_out", allow_f64=True)
+    if rcode != PSVD_F64 or rr != n or rc_ != n:
+        raise ValueError("R_out: must be an n x n float64 matrix")
+    return _check(load().psvd_parallel_qr_static(p, ld, M, n, code, r, _stream_ptr(stream)),
+                  "psvd_parallel_qr_static")
 
 
 def psvd_parallel_svd(h: int, A, part_offsets, r1: int, r2: int, U_out, L_out) -> int:
