@@ -229,6 +229,23 @@ def rsvd_initialize(A0, K, Omega, q):
     return rsvd_panel(_f64(A0), K, Omega, q)
 
 
+def rsvd_run(batches, K, ff, p, q, seed):
+    """Algorithm 1 whose panel SVDs are the randomized low-rank SVD (Sec. 3.3).
+
+    Batch t (t = 0 is the initialisation) draws its Gaussian test matrix as stream t
+    of the Philox key `seed`: n x l with n = k + B the panel width (k = 0 at t = 0)
+    and l = min(K + p, n), kept modes k1 = min(K, n) (l >= k1)."""
+    U = D = None
+    for t, A in enumerate(batches):
+        A = _f64(A)
+        P = A if U is None else panel(U, D, A, ff)
+        n = P.shape[1]
+        k1 = min(K, n)
+        l = max(min(K + p, n), k1)
+        U, D = rsvd_panel(P, k1, gaussian_matrix(seed, t, n, l), q)
+    return U, D
+
+
 def philox4x32(ctr, key, rounds=10):
     lib = _load()
     c = (C.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in ctr])

@@ -437,7 +437,11 @@ static int orthonormalise(int64_t m, int64_t n, double* Y, int64_t ldy) {
  * iteration: Y = P Omega (Omega: n x l Gaussian), Q = orth(Y); q times:
  * Q^ = orth(P^T Q), Q = orth(P Q^).  Then Bm = Q^T P (l x n), SVD of Bm by
  * Jacobi on the columns of Bm^T (Bm^T V' = Z, so U~ = V'), sorted, and
- * U = Q U~_K, D = sigma_K.  P is not modified.  Requires K <= l <= n <= m. */
+ * U = Q U~_K, D = sigma_K.  The sign of each kept mode u_j is fixed so that
+ * (P 1)^T u_j >= 0 (the paper leaves signs free; with a fixed Omega the next
+ * randomized update depends on them, so a convention makes the streamed result
+ * a function of the data and the seed alone).  P is not modified.  Requires
+ * K <= l <= n <= m. */
 int orc_rsvd_panel(int64_t m, int64_t n, const double* P, int64_t ldp, int64_t K, int64_t l,
                    const double* Omega, int64_t ldo, int64_t q, double* U, int64_t ldu, double* D,
                    int max_sweeps, double tol) {
@@ -472,6 +476,16 @@ int orc_rsvd_panel(int64_t m, int64_t n, const double* P, int64_t ldp, int64_t K
       for (int64_t i = 0; i < l; ++i) Uk[IDX(i, j, l)] = Vp[IDX(i, order[j], l)];
     }
     matmul(m, l, K, Y, m, Uk, l, U, ldu); /* U = Q U~_K */
+    /* sign convention: (P 1)^T u_j >= 0 for every kept mode j (Y reused for P 1) */
+    for (int64_t i = 0; i < m; ++i) {
+      double rowsum = 0.0;
+      for (int64_t c = 0; c < n; ++c) rowsum += P[IDX(i, c, ldp)];
+      Y[i] = rowsum;
+    }
+    for (int64_t j = 0; j < K; ++j) {
+      if (dot_col(m, Y, &U[IDX(0, j, ldu)]) < 0.0)
+        for (int64_t i = 0; i < m; ++i) U[IDX(i, j, ldu)] = -U[IDX(i, j, ldu)];
+    }
   }
   free(Y); free(Z); free(Bt); free(Vp); free(s); free(order); free(Uk);
   return rc;

@@ -240,6 +240,11 @@ def test_rsvd_exact_when_sketch_covers_rank(q):
     Ud, Dd = oracle.stream_update(U, D, bs[1], 0.95)
     assert rel_err(Dr, Dd).max() <= 1e-10
     assert max_principal_angle(Ur, Ud) <= 1e-9
+    # sign convention of the randomized modes: (P 1)^T u_j >= 0
+    assert np.all(P.sum(axis=1) @ Ur >= 0.0)
+    # ... and otherwise the same vectors as the exact update (distinct sigmas)
+    sg = np.sign(np.sum(Ur * Ud, axis=0))
+    assert np.abs(Ur - Ud * sg[None, :]).max() <= 1e-8
 
 
 def test_rsvd_power_iteration_improves_accuracy():
@@ -251,6 +256,17 @@ def test_rsvd_power_iteration_improves_accuracy():
     e0 = rel_err(oracle.rsvd_panel(P, 10, Om, 0)[1], ref).max()
     e2 = rel_err(oracle.rsvd_panel(P, 10, Om, 2)[1], ref).max()
     assert e2 < e0 and e2 < 0.05
+
+
+def test_rsvd_run_with_full_sketch_equals_exact_stream():
+    # p >= B gives l = n at every batch: Q spans the whole panel, so each
+    # randomized update reduces to the exact one
+    A, _, _, _ = synthetic.low_rank(300, 60, 30, 1e-6, seed=19, s=[0.8 ** i for i in range(30)])
+    bs = _batches(A.numpy(), 15)
+    Ur, Dr = oracle.rsvd_run(bs, 6, 0.9, p=15, q=0, seed=3)
+    Ud, Dd = oracle.stream_run(bs, 6, 0.9)
+    assert rel_err(Dr, Dd).max() <= 1e-10
+    assert max_principal_angle(Ur, Ud) <= 1e-8
 
 
 # --------------------------------------------------------------------- Philox
