@@ -85,10 +85,13 @@ typedef struct {
   double ff;          /* forget factor in (0, 1] (Sec. 3.1): scales U*D, i.e. sigma */
   int32_t precision;  /* psvd_precision */
   int32_t low_rank;   /* 1: the SVD of each panel is the randomized low-rank SVD
-                         of Sec. 3.3 (range finder Y = P*Omega); 0: exact */
-  int32_t oversample; /* p: the sketch has l = K + p columns (low_rank only) */
-  int32_t power_iters;/* q: power iterations of the range finder (low_rank only) */
-  uint64_t seed;      /* Philox4x32-10 key of the Gaussian sketches */
+                         of Sec. 3.3 (range finder Y = P*Omega, Omega Gaussian
+                         n x l, n = k + B); 0: exact.  Any precision. */
+  int32_t oversample; /* p >= 0: the sketch has l = min(K + p, k + B) columns */
+  int32_t power_iters;/* q in [0, 16]: power iterations of the range finder */
+  uint64_t seed;      /* Philox4x32-10 key of the Gaussian sketches: the sketch of
+                         batch t (t = 0 for psvd_initialize) is
+                         psvd_gaussian_sketch(seed, t, n, l) */
   void* stream;       /* cudaStream_t the handle enqueues on; NULL = default stream */
 } psvd_config;
 

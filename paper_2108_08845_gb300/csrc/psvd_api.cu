@@ -39,6 +39,8 @@ struct psvd_ctx {
   int64_t partial_cap = 0;  // doubles
   double* G = nullptr;
   SmallWork w{};
+  RandWork rw{};  // randomized range finder (low_rank handles only)
+  int lmax = 0;   // sketch columns K + p, capped at K + max_batch
   void* staging = nullptr;
   size_t staging_bytes = 0;
   float* Uf32_tmp = nullptr;  // FP32 view of hi/lo modes for get_modes / save
@@ -220,19 +222,29 @@ int step(psvd_ctx* h, const void* A, int64_t lda, int B, int dtype) {
   w.Dnew = Dnext;
   pr = prof_begin(h, 1);
   int nl = 0;
-  CK(small_solve_launch(w, n, kc, k1, Dcur, h->cfg.ff, /*refine_steps=*/3, /*max_sweeps=*/12,
-                        h->st, &nl));
+  const float* T = w.T;
+  if (h->cfg.low_rank) {
+    // Sec. 3.3: randomized rank-k1 SVD of the panel, sketch stream = batch index
+    int l = (h->lmax < n) ? h->lmax : n;
+    if (l < k1) l = k1;
+    CK(randomized_solve_launch(h->rw, w, n, kc, k1, l, h->cfg.power_iters, Dcur, h->cfg.ff,
+                               h->cfg.seed, (uint64_t)h->iteration, h->st, &nl));
+    T = h->rw.Tupd;
+  } else {
+    CK(small_solve_launch(w, n, kc, k1, Dcur, h->cfg.ff, /*refine_steps=*/3, /*max_sweeps=*/12,
+                          h->st, &nl));
+  }
   prof_end(h, pr);
   h->launches += nl;
   pr = prof_begin(h, 2);
   if (use_tc(h)) {
-    int rc = tc_update(h->Uh[h->cur], h->Ul[h->cur], h->ldu, kc, A, lda, B, dtype, h->M, w.T, n,
+    int rc = tc_update(h->Uh[h->cur], h->Ul[h->cur], h->ldu, kc, A, lda, B, dtype, h->M, T, n,
                        k1, w.T3, h->Uh[h->cur ^ 1], h->Ul[h->cur ^ 1], h->num_sms, &h->w.info[2],
                        h->st);
     if (rc) return rc;
   } else {
     PanelF32 p{h->U[h->cur], h->ldu, kc, A, lda, dtype == PSVD_BF16 ? 1 : 0, h->M, n};
-    CK(update_simt_launch(p, w.T, k1, h->U[h->cur ^ 1], h->ldu, h->st));
+    CK(update_simt_launch(p, T, k1, h->U[h->cur ^ 1], h->ldu, h->st));
   }
   prof_end(h, pr);
   h->launches += use_tc(h) ? 2 : 1;
@@ -297,7 +309,9 @@ int psvd_create(psvd_handle* out, const psvd_config* cfg) {
   if (cfg->precision == PSVD_PREC_BF16_TC &&
       (cfg->K > 80 || ((2 * ((cfg->K + 7) & ~7) + ((cfg->max_batch + 7) & ~7) + 15) & ~15) > 256))
     return PSVD_ERR_SHAPE;
-  if (cfg->low_rank) return PSVD_ERR_UNSUPPORTED;
+  if (cfg->low_rank != 0 &&
+      (cfg->low_rank != 1 || cfg->oversample < 0 || cfg->power_iters < 0 || cfg->power_iters > 16))
+    return PSVD_ERR_INVALID_ARG;
   psvd_ctx* h = new (std::nothrow) psvd_ctx();
   if (!h) return PSVD_ERR_ALLOC;
   h->cfg = *cfg;
@@ -339,6 +353,21 @@ int psvd_create(psvd_handle* out, const psvd_config* cfg) {
   if (!rc) rc = dalloc(&h->w.T, nm * (size_t)h->K);
   if (!rc) rc = dalloc(&h->w.T3, tc_t3_elems(h->K, h->maxB));
   if (!rc) rc = dalloc(&h->w.info, 4);
+  if (!rc && cfg->low_rank) {
+    const int64_t l = (int64_t)cfg->K + cfg->oversample;
+    h->lmax = (int)((l < h->nmax) ? l : h->nmax);
+    const size_t nl = nm * (size_t)h->lmax, ll = (size_t)h->lmax * h->lmax;
+    rc = dalloc(&h->rw.Om, nl);
+    for (int b = 0; b < 3 && !rc; ++b) rc = dalloc(&h->rw.B[b], nl);
+    if (!rc) rc = dalloc(&h->rw.Mm, ll);
+    if (!rc) rc = dalloc(&h->rw.Rr, ll);
+    if (!rc) rc = dalloc(&h->rw.Aw, ll);
+    if (!rc) rc = dalloc(&h->rw.piv, (size_t)h->lmax);
+    if (!rc) rc = dalloc(&h->rw.rank, 1);
+    if (!rc) rc = dalloc(&h->rw.Bb, ll);
+    if (!rc) rc = dalloc(&h->rw.Tupd, nm * (size_t)h->K);
+    if (!rc) rc = dalloc(&h->rw.sgn, (size_t)h->K);
+  }
   if (!rc && cudaMemsetAsync(h->w.info, 0, sizeof(int) * 4, h->st) != cudaSuccess) rc = PSVD_ERR_CUDA;
   if (!rc) {
     // zero the mode buffers once so that padded rows stay zero
@@ -389,6 +418,16 @@ void psvd_destroy(psvd_handle h) {
   cudaFree(h->w.T);
   cudaFree(h->w.T3);
   cudaFree(h->w.info);
+  cudaFree(h->rw.Om);
+  for (int b = 0; b < 3; ++b) cudaFree(h->rw.B[b]);
+  cudaFree(h->rw.Mm);
+  cudaFree(h->rw.Rr);
+  cudaFree(h->rw.Aw);
+  cudaFree(h->rw.piv);
+  cudaFree(h->rw.rank);
+  cudaFree(h->rw.Bb);
+  cudaFree(h->rw.Tupd);
+  cudaFree(h->rw.sgn);
   cudaFree(h->staging);
   cudaFree(h->Uf32_tmp);
   cudaGetLastError();

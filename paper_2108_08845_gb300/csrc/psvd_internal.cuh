@@ -72,8 +72,33 @@ struct SmallWork {
 cudaError_t small_solve_launch(const SmallWork& w, int n, int kc, int k1, const double* D,
                                double ff, int refine_steps, int max_sweeps, cudaStream_t st,
                                int* launches);
+// C (m x nn) = alpha * op(A) * B + beta * Cin (FP64, column-major), op(A) = A or A^T.
+cudaError_t dgemm_launch(bool trans_a, int m, int nn, int k, double alpha, const double* A, int lda,
+                         const double* B, int ldb, double beta, const double* Cin, int ldci,
+                         double* C, int ldc, cudaStream_t st);
 // FP64 Cholesky R^T R = G (n x n) into R (ld n, upper); info[2] = status.
 cudaError_t cholesky_launch(const double* G, int n, double* R, int* info, cudaStream_t st);
+
+// ------------------------------------------------- randomized range finder
+struct RandWork {
+  float* Om;      // n x l Gaussian sketch (FP32)
+  double* B[3];   // n x l FP64 coefficient bases / products
+  double* Mm;     // l x l metric Gram of a basis
+  double* Rr;     // l x l pivoted Cholesky factor (row k, original column j)
+  double* Aw;     // l x l working matrix (used when l exceeds the shared-memory limit)
+  int* piv;       // l pivot order
+  int* rank;      // 1 numerical rank of the last pivoted Cholesky
+  double* Bb;     // l x l  B B^T of the projected panel
+  float* Tupd;    // n x K FP32 update coefficients (ld n)
+  double* sgn;    // K signs of the new modes
+};
+// Randomized rank-k1 SVD of the panel whose scaled Gram H = S G S sits in w.H
+// (n x n): Gaussian sketch of l columns (Philox stream sketch_id), q power
+// iterations; writes the update coefficients r.Tupd (U_new = [U | A] T_upd) and
+// the singular values w.Dnew.  Uses w's eigen-solver scratch.
+cudaError_t randomized_solve_launch(const RandWork& r, const SmallWork& w, int n, int kc, int k1,
+                                    int l, int q, const double* D, double ff, uint64_t seed,
+                                    uint64_t sketch_id, cudaStream_t st, int* launches);
 
 // -------------------------------------------------------------------- Philox
 cudaError_t gaussian_sketch_launch(uint64_t seed, uint64_t stream_id, int64_t rows, int64_t cols,

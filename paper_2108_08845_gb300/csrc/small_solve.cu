@@ -469,6 +469,13 @@ cudaError_t small_solve_launch(const SmallWork& w, int n, int kc, int k1, const 
   return cudaGetLastError();
 }
 
+cudaError_t dgemm_launch(bool trans_a, int m, int nn, int k, double alpha, const double* A, int lda,
+                         const double* B, int ldb, double beta, const double* Cin, int ldci,
+                         double* C, int ldc, cudaStream_t st) {
+  return trans_a ? dgemm<true>(m, nn, k, alpha, A, lda, B, ldb, beta, Cin, ldci, C, ldc, st)
+                 : dgemm<false>(m, nn, k, alpha, A, lda, B, ldb, beta, Cin, ldci, C, ldc, st);
+}
+
 cudaError_t cholesky_launch(const double* G, int n, double* R, int* info, cudaStream_t st) {
   cholesky_kernel<<<1, 256, 0, st>>>(G, n, R, info);
   return cudaGetLastError();
