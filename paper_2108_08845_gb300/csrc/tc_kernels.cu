@@ -39,6 +39,12 @@ namespace {
 constexpr int kRowsStage = 64;            // rows per Gram stage (one 128-byte swizzle row per column)
 constexpr int kSlab = 128;                // panel columns per MMA slab (UMMA M)
 constexpr int kGramStages = 6;
+// 64-row stages per FP32 accumulation chain before it is folded into the
+// float-float totals.  The tensor-core FP32 accumulation has a relative bias that
+// grows with the chain (measured about -1.5e-8 per MMA on the Gram diagonal); with
+// 2 stages (8 MMAs) the 64-mode subspace of the config-3 recipe stays within
+// 5.3e-4 rad of the FP64 result (2.2e-3 with 4 stages), at the same Gram time.
+constexpr int kFoldStages = 2;
 constexpr int kUpdRows = 128;             // rows per update tile (UMMA M)
 constexpr int kUpdStages = 2;
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
@@ -772,9 +778,7 @@ GramGeom gram_geom(int64_t M, int kc, int B, int num_sms) {
   if (rr < kRowsStage) rr = kRowsStage;
   g.range_rows = rr;
   g.nrange = ceil_div(M, rr);
-  const char* fs = getenv("PSVD_TC_FOLD_STAGES");  // experiment hook
-  g.fold_stages = fs ? atoi(fs) : 4;
-  if (g.fold_stages < 1) g.fold_stages = 1;
+  g.fold_stages = kFoldStages;
   return g;
 }
 
