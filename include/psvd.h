@@ -204,10 +204,10 @@ int psvd_get_profile(psvd_handle h, double* ms_out, int64_t* count_out, int64_t*
 const char* psvd_status_string(int status);
 
 /* psvd_last_info: diagnostics of the most recent update (synchronises): info4[0]
- * and info4[1] are the Jacobi sweeps of the two FP32 stages of the small
- * eigen-solve, info4[2] the accumulated status bits since psvd_initialize
- * (1 rank deficient, 2 not converged, 4 non-finite), info4[3] the kept mode
- * count.  info4 is a host int32[4]. */
+ * is the number of scale levels of the small eigen-solve, info4[1] the leading
+ * eigenpairs they resolved before refinement, info4[2] the accumulated status
+ * bits since psvd_initialize (1 rank deficient, 2 not converged, 4 non-finite,
+ * 8 timeout), info4[3] the kept mode count.  info4 is a host int32[4]. */
 int psvd_last_info(psvd_handle h, int32_t* info4);
 
 #ifdef __cplusplus

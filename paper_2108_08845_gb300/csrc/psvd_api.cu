@@ -231,7 +231,7 @@ int step(psvd_ctx* h, const void* A, int64_t lda, int B, int dtype) {
                                h->cfg.seed, (uint64_t)h->iteration, h->st, &nl));
     T = h->rw.Tupd;
   } else {
-    CK(small_solve_launch(w, n, kc, k1, Dcur, h->cfg.ff, /*refine_steps=*/3, /*max_sweeps=*/12,
+    CK(small_solve_launch(w, n, kc, k1, Dcur, h->cfg.ff, /*refine_steps=*/3, kMaxLevels,
                           h->st, &nl));
   }
   prof_end(h, pr);
@@ -353,6 +353,8 @@ int psvd_create(psvd_handle* out, const psvd_config* cfg) {
   if (!rc) rc = dalloc(&h->w.T, nm * (size_t)h->K);
   if (!rc) rc = dalloc(&h->w.T3, tc_t3_elems(h->K, h->maxB));
   if (!rc) rc = dalloc(&h->w.info, 4);
+  if (!rc) rc = dalloc(&h->w.fs, eig_levels_scratch_floats(h->nmax));
+  if (!rc) rc = dalloc(reinterpret_cast<char**>(&h->w.ls), sizeof(LevelState));
   if (!rc && cfg->low_rank) {
     const int64_t l = (int64_t)cfg->K + cfg->oversample;
     h->lmax = (int)((l < h->nmax) ? l : h->nmax);
@@ -418,6 +420,8 @@ void psvd_destroy(psvd_handle h) {
   cudaFree(h->w.T);
   cudaFree(h->w.T3);
   cudaFree(h->w.info);
+  cudaFree(h->w.fs);
+  cudaFree(h->w.ls);
   cudaFree(h->rw.Om);
   for (int b = 0; b < 3; ++b) cudaFree(h->rw.B[b]);
   cudaFree(h->rw.Mm);

@@ -14,6 +14,8 @@ namespace psvd {
 constexpr int kMaxN = 192;
 // Extra eigenpairs refined beyond the kept K (covers the truncation boundary).
 constexpr int kRefineMargin = 8;
+// Scale levels of the small eigen-solve launched per update (device-side early exit).
+constexpr int kMaxLevels = 8;
 
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -49,6 +51,18 @@ cudaError_t update_simt_launch(const PanelF32& p, const float* T, int k1, float*
                                int64_t ldo, cudaStream_t st);
 
 // ------------------------------------------------------------- small solve
+// Device-side progress of the level-by-level eigen-solve (small_eig.cu).
+struct LevelState {
+  int b;        // leading eigenpairs resolved so far
+  int b0;       // first column of the block the last level solved
+  int active;   // 1 while another level is needed
+  int skip;     // 1 when the last level kernel produced no transform
+  int r;        // eigenpairs resolved by the last level
+  int levels;   // levels run
+  int floored;  // 1 when the levels stopped at the resolution floor
+  double lmax;  // largest eigenvalue of H
+};
+
 struct SmallWork {
   double* H;      // n x n FP64 (scaled Gram), ld n
   double* X;      // n x n FP64 eigenvector estimates (sorted), ld n
@@ -62,7 +76,9 @@ struct SmallWork {
   float* T;       // n x K FP32 update coefficients
   __nv_bfloat16* T3;  // (3 n) x K BF16 triple split of T (tensor-core path)
   double* Dnew;   // K new singular values
-  int* info;      // device int[4]: sweeps, refine steps, status, k1
+  int* info;      // device int[4]: levels, resolved count, status, k1
+  LevelState* ls; // level-solve progress
+  float* fs;      // FP32 scratch of the level solve (eig_levels_scratch_floats)
 };
 
 // Eigen-decomposition of H (n x n) and the update coefficients:
@@ -70,8 +86,19 @@ struct SmallWork {
 //   T = S X[:, 0:k1] diag(1/sigma), Dnew = sigma.
 // *launches receives the number of kernels enqueued.
 cudaError_t small_solve_launch(const SmallWork& w, int n, int kc, int k1, const double* D,
-                               double ff, int refine_steps, int max_sweeps, cudaStream_t st,
+                               double ff, int refine_steps, int max_levels, cudaStream_t st,
                                int* launches);
+// Eigenvectors and eigenvalues of H (n x n, w.H) by FP32 tridiagonal solves on
+// successive scale levels with FP64 projections between them: w.X (n x n) holds
+// the basis, w.lam the eigenvalue estimates (descending); the leading nJ are
+// resolved to ~u32 / 1e-3 relative accuracy.  Uses w.W, w.S, w.R, w.Xn, w.fs, w.ls.
+cudaError_t eig_levels_launch(const SmallWork& w, int n, int nJ, int max_levels, cudaStream_t st,
+                              int* launches);
+size_t eig_levels_scratch_floats(int nmax);
+// C (m x nn) = op(A) * B (FP64) if *flag != 0, otherwise nothing.
+cudaError_t dgemm_flag_launch(bool trans_a, int m, int nn, int k, const double* A, int lda,
+                              const double* B, int ldb, double* C, int ldc, const int* flag,
+                              cudaStream_t st);
 // C (m x nn) = alpha * op(A) * B + beta * Cin (FP64, column-major), op(A) = A or A^T.
 cudaError_t dgemm_launch(bool trans_a, int m, int nn, int k, double alpha, const double* A, int lda,
                          const double* B, int ldb, double beta, const double* Cin, int ldci,

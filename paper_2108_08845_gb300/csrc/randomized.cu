@@ -264,7 +264,7 @@ cudaError_t randomized_solve_launch(const RandWork& r, const SmallWork& w, int n
   SmallWork wb = w;
   wb.H = r.Bb;
   int ns = 0;
-  RCK(small_solve_launch(wb, l, 0, k1, nullptr, 1.0, /*refine_steps=*/3, /*max_sweeps=*/12, st,
+  RCK(small_solve_launch(wb, l, 0, k1, nullptr, 1.0, /*refine_steps=*/3, kMaxLevels, st,
                          &ns));
   nl += ns;
   sign_kernel<<<1, 256, 0, st>>>(B2, n, l, k1, w.T, r.sgn);

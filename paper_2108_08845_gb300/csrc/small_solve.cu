@@ -7,17 +7,11 @@
 //
 // The eigen-solve is built for a GPU whose FP64 rate is ~2 FMA/clk/SM (FP32
 // ~114): O(n^3) FP64 work only appears as small GEMMs spread over all SMs.
-//   1. jacobi_eig_kernel on H: cyclic two-sided Jacobi in FP32 on one CTA (packed
-//      symmetric matrix and eigenvector matrix in shared memory, round-robin
-//      parallel ordering: n/2 disjoint rotations per round).  Eigenvalues that
-//      arise by cancellation between columns are only resolved to ~u32 ||H||.
-//   2. H2 = X1^T H X1 in FP64 (GEMMs).  H2 is graded: the resolved part is
-//      nearly diagonal and the unresolved part is a block of size ~u32 ||H||.
-//   3. jacobi_eig_kernel on H2 in FP32; on a graded matrix two-sided Jacobi is
-//      relatively accurate (Demmel & Veselic, 1992), so the combined basis
-//      X = X1 X2 is accurate to ~u32^2 ||H|| in absolute terms.
-//   4. Ogita & Aishima (2018) iterative refinement (RefSyEv) of the leading
-//      eigenpairs in FP64 (GEMMs), quadratically convergent from X.
+//   1. eig_levels_launch (small_eig.cu): FP32 tridiagonal solves on successive
+//      scale levels, FP64 projections between them; the leading eigenpairs come
+//      out accurate to ~u32 / 1e-3 relative to their own size.
+//   2. Ogita & Aishima (2018) iterative refinement (RefSyEv) of the leading
+//      eigenpairs in FP64 (GEMMs), quadratically convergent from there.
 // finalize_kernel sorts, truncates to k1 and forms T = S V_k1 diag(1/sigma).
 #include <math.h>
 
@@ -26,7 +20,6 @@
 namespace psvd {
 namespace {
 
-constexpr int JT = 1024;
 // Resolution of a Gram-based factorisation: eigenvalues of the scaled Gram below
 // kLambdaFloor * lambda_max (singular values below sqrt of that times sigma_max)
 // are at the rounding level of the Gram and are not resolved; such kept modes
@@ -38,173 +31,17 @@ constexpr double kSigmaFloor = 3.1622776601683795e-5;  // sqrt(kLambdaFloor)
 // by the callers), so descending ranks are always a permutation.
 __device__ __forceinline__ double sort_key(double x) { return isnan(x) ? -INFINITY : x; }
 
-__device__ __forceinline__ int pidx(int i, int j) {  // packed upper, i <= j
-  return j * (j + 1) / 2 + i;
-}
-__device__ __forceinline__ int pidx_any(int a, int b) { return a <= b ? pidx(a, b) : pidx(b, a); }
-
-// Round-robin ("circle") tournament on N (even) players: in round r player N-1
-// sits at position 0 and player (k - 1 + r) mod (N - 1) at position k >= 1;
-// pair i meets positions i and N-1-i.  Every pair meets once per N-1 rounds.
-__device__ __forceinline__ int tour_player(int pos, int r, int N) {
-  return pos == 0 ? N - 1 : (pos - 1 + r) % (N - 1);
-}
-
-__global__ void __launch_bounds__(JT) jacobi_eig_kernel(const double* __restrict__ H, int n,
-                                                        double* __restrict__ X,
-                                                        double* __restrict__ lam, int max_sweeps,
-                                                        float tol, int* __restrict__ info,
-                                                        int info_slot, int flag_unconverged,
-                                                        const double* __restrict__ ref_lam,
-                                                        int ref_idx, double ref_frac) {
-  extern __shared__ __align__(16) float sm[];
-  __shared__ float cs_c[kMaxN / 2], cs_s[kMaxN / 2];
-  __shared__ int pp[kMaxN / 2], qq[kMaxN / 2];
-  __shared__ int rot_any, rot_flag[2];
-  __shared__ float dmax;
-  __shared__ int rank_of[kMaxN];
-  const int N = (n + 1) & ~1;
-  const int P = N / 2;
-  const int LDV = (N + 3) & ~3;  // 16-byte aligned eigenvector columns
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int npk = ((N * (N + 1) / 2) + 3) & ~3;
-  float* Hp = sm;        // packed upper triangle of the working matrix
-  float* V = sm + npk;   // N x N eigenvector matrix, column-major, ld LDV
-
-  for (int e = tid; e < N * N; e += JT) {
-    const int i = e % N, j = e / N;
-    if (i <= j) Hp[pidx(i, j)] = (i < n && j < n) ? (float)H[i + (int64_t)j * n] : 0.f;
-    V[i + j * LDV] = (i == j) ? 1.f : 0.f;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    float m = 0.f;
-    for (int i = 0; i < n; ++i) m = fmaxf(m, fabsf(Hp[pidx(i, i)]));
-    dmax = m;
-    rot_flag[0] = rot_flag[1] = 0;
-  }
-  __syncthreads();
-  // Pairs whose diagonal entries are both below floor_d are not rotated: below
-  // the Gram's resolution (kLambdaFloor * lambda_max) they carry no information,
-  // and with ref_lam (eigenvalue estimates from a previous stage) directions far
-  // below the ref_idx-th eigenvalue need not be separated from each other (the
-  // refinement only needs them as an orthonormal complement of the kept modes).
-  float floor_d = (float)kLambdaFloor * dmax;
-  if (ref_lam) floor_d = fmaxf(floor_d, (float)(ref_frac * ref_lam[ref_idx]));
-
-  int sweep = 0;
-  int gr = 0;  // round counter across sweeps: selects the double-buffered round flag
-  bool converged = false;
-  while (sweep < max_sweeps) {
-    ++sweep;
-    if (tid == 0) rot_any = 0;  // every thread read it before the barrier that ended the last sweep
-    for (int r = 0; r < N - 1; ++r, ++gr) {
-      __syncthreads();
-      // all threads finished the previous round (and read its flag): clear the
-      // flag the next round will use
-      if (tid == 0) rot_flag[(gr + 1) & 1] = 0;
-      // rotation of each disjoint pair (p, q): zeroes H_pq (Golub & Van Loan sym.schur2)
-      if (tid < P) {
-        int p = tour_player(tid, r, N), q = tour_player(N - 1 - tid, r, N);
-        if (p > q) { const int t = p; p = q; q = t; }
-        const float app = Hp[pidx(p, p)], aqq = Hp[pidx(q, q)], apq = Hp[pidx(p, q)];
-        float c = 1.f, s = 0.f;
-        if (apq != 0.f && (fabsf(app) > floor_d || fabsf(aqq) > floor_d) &&
-            fabsf(apq) > tol * sqrtf(fabsf(app)) * sqrtf(fabsf(aqq))) {
-          const float th = (aqq - app) / (2.f * apq);
-          const float at = fabsf(th);
-          float t = (at > 1e18f) ? 0.5f / at : 1.f / (at + sqrtf(1.f + th * th));
-          t = (th >= 0.f) ? t : -t;
-          c = rsqrtf(1.f + t * t);
-          s = t * c;
-          Hp[pidx(p, p)] = app - t * apq;
-          Hp[pidx(q, q)] = aqq + t * apq;
-          Hp[pidx(p, q)] = 0.f;
-          rot_any = 1;
-          rot_flag[gr & 1] = 1;
-        }
-        pp[tid] = p;
-        qq[tid] = q;
-        cs_c[tid] = c;
-        cs_s[tid] = s;
-      }
-      __syncthreads();
-      if (!rot_flag[gr & 1]) continue;  // no pair rotated in this round: nothing to apply
-      // off-diagonal 2x2 blocks B_kl <- J_k^T B_kl J_l, k < l: warp w takes block
-      // rows k = w, w+32, ..., its lanes the columns l > k
-      for (int k = warp; k < P; k += JT / 32) {
-        const float sk = cs_s[k], ck = cs_c[k];
-        const int pk = pp[k], qk = qq[k];
-        for (int l = k + 1 + lane; l < P; l += 32) {
-          const float sl = cs_s[l];
-          if (sk == 0.f && sl == 0.f) continue;
-          const float cl = cs_c[l];
-          const int pl = pp[l], ql = qq[l];
-          const int i11 = pidx_any(pk, pl), i12 = pidx_any(pk, ql), i21 = pidx_any(qk, pl),
-                    i22 = pidx_any(qk, ql);
-          const float x11 = Hp[i11], x12 = Hp[i12], x21 = Hp[i21], x22 = Hp[i22];
-          const float y11 = ck * x11 - sk * x21, y12 = ck * x12 - sk * x22;
-          const float y21 = sk * x11 + ck * x21, y22 = sk * x12 + ck * x22;
-          Hp[i11] = cl * y11 - sl * y12;
-          Hp[i12] = sl * y11 + cl * y12;
-          Hp[i21] = cl * y21 - sl * y22;
-          Hp[i22] = sl * y21 + cl * y22;
-        }
-      }
-      // eigenvector columns V <- V J, four rows per item
-      const int nq = LDV / 4;
-      for (int e = tid; e < P * nq; e += JT) {
-        const int k = e / nq, c4 = e - k * nq;
-        const float s = cs_s[k];
-        if (s == 0.f) continue;
-        const float c = cs_c[k];
-        float4* vp = reinterpret_cast<float4*>(&V[pp[k] * LDV]) + c4;
-        float4* vq = reinterpret_cast<float4*>(&V[qq[k] * LDV]) + c4;
-        const float4 a = *vp, b = *vq;
-        *vp = make_float4(c * a.x - s * b.x, c * a.y - s * b.y, c * a.z - s * b.z, c * a.w - s * b.w);
-        *vq = make_float4(s * a.x + c * b.x, s * a.y + c * b.y, s * a.z + c * b.z, s * a.w + c * b.w);
-      }
-    }
-    __syncthreads();
-    const int any = rot_any;
-    __syncthreads();  // every thread has read rot_any before thread 0 resets it
-    if (!any) {
-      converged = true;
-      break;
-    }
-  }
-  __syncthreads();
-  // sort eigenvalues descending (stable on index) and write FP64 outputs
-  if (tid < n) {
-    const float li = Hp[pidx(tid, tid)];
-    const double ki = sort_key((double)li);
-    int rank = 0;
-    for (int j = 0; j < n; ++j) {
-      const double kj = sort_key((double)Hp[pidx(j, j)]);
-      rank += (kj > ki) || (kj == ki && j < tid);
-    }
-    rank_of[tid] = rank;
-    lam[rank] = (double)li;
-  }
-  __syncthreads();
-  for (int e = tid; e < n * n; e += JT) {
-    const int i = e % n, j = e / n;
-    X[i + (int64_t)rank_of[j] * n] = (double)V[i + j * LDV];
-  }
-  if (tid == 0) {
-    info[info_slot] = sweep;
-    if (!converged && flag_unconverged) atomicOr(&info[2], 2);
-  }
-}
-
 // C (m x nn) = alpha * op(A) * B + beta * Cin, FP64, column-major.
 // op(A) = A (lda >= m) or A^T (A is k x m).  8 x 8 outputs per CTA.
+// With flag != nullptr the kernel does nothing while *flag == 0.
 template <bool TRANS_A>
 __global__ void __launch_bounds__(64) dgemm_kernel(int m, int nn, int k, double alpha,
                                                    const double* __restrict__ A, int lda,
                                                    const double* __restrict__ B, int ldb,
                                                    double beta, const double* __restrict__ Cin,
-                                                   int ldci, double* __restrict__ C, int ldc) {
+                                                   int ldci, double* __restrict__ C, int ldc,
+                                                   const int* __restrict__ flag) {
+  if (flag && *flag == 0) return;
   __shared__ double As[8][33];
   __shared__ double Bs[32][9];
   const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
@@ -406,47 +243,34 @@ __global__ void cholesky_kernel(const double* __restrict__ G, int n, double* __r
 template <bool TA>
 cudaError_t dgemm(int m, int nn, int k, double alpha, const double* A, int lda, const double* B,
                   int ldb, double beta, const double* Cin, int ldci, double* C, int ldc,
-                  cudaStream_t st) {
+                  cudaStream_t st, const int* flag = nullptr) {
   dim3 grid((unsigned)ceil_div(m, 8), (unsigned)ceil_div(nn, 8));
-  dgemm_kernel<TA><<<grid, 64, 0, st>>>(m, nn, k, alpha, A, lda, B, ldb, beta, Cin, ldci, C, ldc);
+  dgemm_kernel<TA><<<grid, 64, 0, st>>>(m, nn, k, alpha, A, lda, B, ldb, beta, Cin, ldci, C, ldc,
+                                        flag);
   return cudaGetLastError();
+}
+
+// info[0] = levels, info[1] = leading eigenpairs resolved; bit 2 when the levels
+// ended before resolving nJ eigenpairs above the resolution floor.
+__global__ void level_info_kernel(const LevelState* __restrict__ ls, int nJ, int* __restrict__ info) {
+  info[0] = ls->levels;
+  info[1] = ls->b;
+  if (ls->b < nJ && !ls->floored) atomicOr(&info[2], 2);
 }
 
 }  // namespace
 
-size_t jacobi_smem_bytes(int n) {
-  const int N = (n + 1) & ~1;
-  const int npk = ((N * (N + 1) / 2) + 3) & ~3;
-  const int ldv = (N + 3) & ~3;
-  return sizeof(float) * ((size_t)npk + (size_t)N * ldv);
-}
-
 cudaError_t small_solve_launch(const SmallWork& w, int n, int kc, int k1, const double* D,
-                               double ff, int refine_steps, int max_sweeps, cudaStream_t st,
+                               double ff, int refine_steps, int max_levels, cudaStream_t st,
                                int* launches) {
-  *launches = 5 + 6 * refine_steps + 2 + 1;
-  const size_t smem = jacobi_smem_bytes(n);
-  cudaError_t e = cudaFuncSetAttribute(jacobi_eig_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  // stage 1: FP32 Jacobi on H -> X1 (in E), eigenvalues (in lamJ, unused)
-  // stage 1 only has to reach the FP32 rounding floor; stage 2 does the rest
-  const int stage1_sweeps = (max_sweeps < 3) ? max_sweeps : 3;
-  jacobi_eig_kernel<<<1, JT, smem, st>>>(w.H, n, w.E, w.lamJ, stage1_sweeps, 2e-6f, w.info, 0, 0,
-                                          nullptr, 0, 0.0);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  // stage 2: H2 = X1^T H X1 (FP64, in S), FP32 Jacobi on H2 -> X2 (in R), lam
-  if ((e = dgemm<false>(n, n, n, 1.0, w.H, n, w.E, n, 0.0, nullptr, n, w.W, n, st))) return e;
-  if ((e = dgemm<true>(n, n, n, 1.0, w.E, n, w.W, n, 0.0, nullptr, n, w.S, n, st))) return e;
-  // stage 2 stops at relative off-diagonals of 1e-4: the FP64 refinement that
-  // follows is quadratically convergent from there
-  const int nJ0 = (k1 + kRefineMargin < n) ? k1 + kRefineMargin : n;
-  jacobi_eig_kernel<<<1, JT, smem, st>>>(w.S, n, w.R, w.lam, max_sweeps, 1e-4f, w.info, 1, 1,
-                                          w.lamJ, nJ0 - 1, 1e-2);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  // X = X1 X2
-  if ((e = dgemm<false>(n, n, n, 1.0, w.E, n, w.R, n, 0.0, nullptr, n, w.X, n, st))) return e;
+  cudaError_t e;
   const int nJ = (k1 + kRefineMargin < n) ? k1 + kRefineMargin : n;
+  int nl = 0;
+  // 1. basis X and eigenvalue estimates lam from the scale levels
+  if ((e = eig_levels_launch(w, n, nJ, max_levels, st, &nl)) != cudaSuccess) return e;
+  level_info_kernel<<<1, 1, 0, st>>>(w.ls, nJ, w.info);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // 2. Ogita-Aishima refinement of the leading nJ eigenpairs
   for (int it = 0; it < refine_steps; ++it) {
     // W = H X_J ; S = X^T W ; XtX = X^T X_J
     if ((e = dgemm<false>(n, nJ, n, 1.0, w.H, n, w.X, n, 0.0, nullptr, n, w.W, n, st))) return e;
@@ -466,7 +290,15 @@ cudaError_t small_solve_launch(const SmallWork& w, int n, int kc, int k1, const 
   rayleigh_kernel<<<nJ, 256, 0, st>>>(n, nJ, w.X, w.W, w.lamJ);
   if ((e = cudaGetLastError())) return e;
   finalize_kernel<<<1, 256, 0, st>>>(n, nJ, kc, k1, w.X, w.lamJ, D, ff, w.T, nullptr, w.Dnew, w.info);
+  *launches = nl + 1 + 6 * refine_steps + 3;
   return cudaGetLastError();
+}
+
+cudaError_t dgemm_flag_launch(bool trans_a, int m, int nn, int k, const double* A, int lda,
+                              const double* B, int ldb, double* C, int ldc, const int* flag,
+                              cudaStream_t st) {
+  return trans_a ? dgemm<true>(m, nn, k, 1.0, A, lda, B, ldb, 0.0, nullptr, ldc, C, ldc, st, flag)
+                 : dgemm<false>(m, nn, k, 1.0, A, lda, B, ldb, 0.0, nullptr, ldc, C, ldc, st, flag);
 }
 
 cudaError_t dgemm_launch(bool trans_a, int m, int nn, int k, double alpha, const double* A, int lda,
