@@ -134,8 +134,12 @@ int psvd_parallel_qr(psvd_handle h, const void* P, int64_t ldp, int32_t n, int32
  * part_offsets[0] = 0 and part_offsets[nparts] = Mtot; every block needs
  * >= N rows.  Local right singular vectors (r1 kept per block), gather of
  * W = [V~^1 S~^1, ...], SVD of W (r2 kept), then U~^b_j = A^b X~_j / L~_j.
- * Outputs: U_out (Mtot x r2, FP32, ldu >= Mtot), L_out (r2, FP64), host or
- * device.  N <= 192, r1 <= N, r2 <= min(N, r1*nparts). */
+ * Outputs: U_out (Mtot x r2, FP32, ldu >= Mtot), L_out (r2, FP64, descending),
+ * host or device.  N <= 192, r1 <= N, r2 <= min(N, r1*nparts).  Runs on the
+ * FP32 path for either handle precision and uses the handle only for its
+ * stream and staging buffer; workspace is allocated and freed by the call,
+ * which synchronises the stream.  Returns PSVD_WARN_RANK_DEFICIENT when a kept
+ * L~_j is numerically zero (that mode is returned as zero). */
 int psvd_parallel_svd(psvd_handle h, const void* A, int64_t lda, const int64_t* part_offsets,
                       int32_t nparts, int32_t N, int32_t dtype, int32_t r1, int32_t r2,
                       float* U_out, int64_t ldu, double* L_out);

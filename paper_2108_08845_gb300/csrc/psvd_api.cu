@@ -513,10 +513,47 @@ int psvd_parallel_qr(psvd_handle h, const void* P, int64_t ldp, int32_t n, int32
 int psvd_parallel_svd(psvd_handle h, const void* A, int64_t lda, const int64_t* part_offsets,
                       int32_t nparts, int32_t N, int32_t dtype, int32_t r1, int32_t r2,
                       float* U_out, int64_t ldu, double* L_out) {
-  (void)A; (void)lda; (void)part_offsets; (void)nparts; (void)N; (void)dtype; (void)r1; (void)r2;
-  (void)U_out; (void)ldu; (void)L_out;
-  if (!h) return PSVD_ERR_INVALID_ARG;
-  return PSVD_ERR_UNSUPPORTED;
+  if (!h || !A || !part_offsets || !U_out || !L_out || nparts < 1) return PSVD_ERR_INVALID_ARG;
+  if (dtype != PSVD_F32 && dtype != PSVD_BF16) return PSVD_ERR_INVALID_ARG;
+  if (N < 1 || N > kMaxN || r1 < 1 || r1 > N || r2 < 1 || r2 > N || (int64_t)r2 > (int64_t)r1 * nparts)
+    return PSVD_ERR_SHAPE;
+  if (part_offsets[0] != 0) return PSVD_ERR_INVALID_ARG;
+  for (int b = 0; b < nparts; ++b)
+    if (part_offsets[b + 1] - part_offsets[b] < N) return PSVD_ERR_SHAPE;
+  const int64_t Mtot = part_offsets[nparts];
+  if (lda < Mtot || ldu < Mtot) return PSVD_ERR_INVALID_ARG;
+  const void* Ad;
+  int64_t ldd;
+  if (int rc = stage_input(h, A, lda, Mtot, N, dtype, false, &Ad, &ldd)) return rc;
+  // outputs: device pointers are written in place, host ones through temporaries
+  const bool u_dev = is_device_ptr(U_out), l_dev = is_device_ptr(L_out);
+  float* Ud = U_out;
+  double* Ld = L_out;
+  int64_t ldud = ldu;
+  if (!u_dev) {
+    ldud = Mtot;
+    if (dalloc(&Ud, (size_t)Mtot * r2)) return PSVD_ERR_ALLOC;
+  }
+  if (!l_dev && dalloc(&Ld, (size_t)r2)) {
+    if (!u_dev) cudaFree(Ud);
+    return PSVD_ERR_ALLOC;
+  }
+  int bits = 0;
+  int rc = apmos_run(Ad, ldd, dtype == PSVD_BF16 ? 1 : 0, Mtot, part_offsets, nparts, N, r1, r2,
+                     Ud, ldud, Ld, h->num_sms, h->st, &bits);
+  if (rc == PSVD_OK && !u_dev &&
+      cudaMemcpy2DAsync(U_out, sizeof(float) * ldu, Ud, sizeof(float) * ldud, sizeof(float) * Mtot,
+                        r2, cudaMemcpyDeviceToHost, h->st) != cudaSuccess)
+    rc = PSVD_ERR_CUDA;
+  if (rc == PSVD_OK && !l_dev &&
+      cudaMemcpyAsync(L_out, Ld, sizeof(double) * r2, cudaMemcpyDeviceToHost, h->st) != cudaSuccess)
+    rc = PSVD_ERR_CUDA;
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) rc = PSVD_ERR_CUDA;
+  if (!u_dev) cudaFree(Ud);
+  if (!l_dev) cudaFree(Ld);
+  if (rc != PSVD_OK) return rc;
+  if (bits & 4) return PSVD_ERR_NONFINITE;
+  return (bits & 1) ? PSVD_WARN_RANK_DEFICIENT : PSVD_OK;
 }
 
 int psvd_set_profiling(psvd_handle h, int32_t enable) {

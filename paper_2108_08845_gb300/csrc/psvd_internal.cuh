@@ -79,6 +79,7 @@ struct SmallWork {
   int* info;      // device int[4]: levels, resolved count, status, k1
   LevelState* ls; // level-solve progress
   float* fs;      // FP32 scratch of the level solve (eig_levels_scratch_floats)
+  double* T64;    // optional (may be null): n x K FP64 copy of T
 };
 
 // Eigen-decomposition of H (n x n) and the update coefficients:
@@ -126,6 +127,16 @@ struct RandWork {
 cudaError_t randomized_solve_launch(const RandWork& r, const SmallWork& w, int n, int kc, int k1,
                                     int l, int q, const double* D, double ff, uint64_t seed,
                                     uint64_t sketch_id, cudaStream_t st, int* launches);
+
+// ------------------------------------------------------------------- APMOS
+// Algorithm 2 on device data: A (Mtot x N, lda, FP32 or BF16) in row blocks
+// [off[b], off[b+1]) (host array), r1 local and r2 global modes; U (Mtot x r2,
+// FP32, ldu) and L (r2, FP64) on the device.  *status receives the accumulated
+// status bits (1 rank deficient, 4 non-finite).  Allocates and frees its own
+// workspace; synchronises the stream.
+int apmos_run(const void* A, int64_t lda, int a_bf16, int64_t Mtot, const int64_t* off, int nparts,
+              int N, int r1, int r2, float* U, int64_t ldu, double* L, int num_sms,
+              cudaStream_t st, int* status);
 
 // -------------------------------------------------------------------- Philox
 cudaError_t gaussian_sketch_launch(uint64_t seed, uint64_t stream_id, int64_t rows, int64_t cols,

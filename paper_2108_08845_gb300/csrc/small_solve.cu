@@ -151,7 +151,8 @@ __global__ void copy_cols_kernel(const double* __restrict__ src, double* __restr
 __global__ void finalize_kernel(int n, int nJ, int kc, int k1, const double* __restrict__ X,
                                 const double* __restrict__ lamJ, const double* __restrict__ D,
                                 double ff, float* __restrict__ T, __nv_bfloat16* __restrict__ T3,
-                                double* __restrict__ Dnew, int* __restrict__ info) {
+                                double* __restrict__ T64, double* __restrict__ Dnew,
+                                int* __restrict__ info) {
   __shared__ int order[kMaxN];
   __shared__ double sig[kMaxN], xn[kMaxN];
   const int tid = threadIdx.x;
@@ -197,6 +198,7 @@ __global__ void finalize_kernel(int n, int nJ, int kc, int k1, const double* __r
     const double scale = (i < kc) ? ff * D[i] : 1.0;
     const double t = (s > 0.0) ? scale * X[i + (int64_t)order[k] * n] / (s * xn[k]) : 0.0;
     T[i + (int64_t)k * n] = (float)t;
+    if (T64) T64[i + (int64_t)k * n] = t;
     if (T3) {
       // exact triple split t = h + m + l (24 significant bits) for BF16 operands
       const __nv_bfloat16 h = __float2bfloat16_rn((float)t);
@@ -289,7 +291,8 @@ cudaError_t small_solve_launch(const SmallWork& w, int n, int kc, int k1, const 
   if ((e = dgemm<false>(n, nJ, n, 1.0, w.H, n, w.X, n, 0.0, nullptr, n, w.W, n, st))) return e;
   rayleigh_kernel<<<nJ, 256, 0, st>>>(n, nJ, w.X, w.W, w.lamJ);
   if ((e = cudaGetLastError())) return e;
-  finalize_kernel<<<1, 256, 0, st>>>(n, nJ, kc, k1, w.X, w.lamJ, D, ff, w.T, nullptr, w.Dnew, w.info);
+  finalize_kernel<<<1, 256, 0, st>>>(n, nJ, kc, k1, w.X, w.lamJ, D, ff, w.T, nullptr, w.T64, w.Dnew,
+                                    w.info);
   *launches = nl + 1 + 6 * refine_steps + 3;
   return cudaGetLastError();
 }
