@@ -15,7 +15,7 @@ constexpr int kMaxN = 192;
 // Extra eigenpairs refined beyond the kept K (covers the truncation boundary).
 constexpr int kRefineMargin = 8;
 // Scale levels of the small eigen-solve launched per update (device-side early exit).
-constexpr int kMaxLevels = 8;
+constexpr int kMaxLevels = 4;
 
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 

@@ -33,8 +33,11 @@
 namespace psvd {
 namespace {
 
-constexpr int LT = 1024;          // threads of the level kernel
+constexpr int LT = 512;           // threads of the level kernel (128 registers each)
 constexpr int LW = LT / 32;       // warps
+constexpr int TRR = kMaxN / LW;   // rows of the register tile of a thread (12)
+constexpr int TRC = kMaxN / 32;   // columns of the register tile of a thread (6)
+constexpr int NB3 = kMaxN / (LT / 8);  // eigenvalues per thread in the multisection (3)
 constexpr int LWI = 8;            // warps running inverse iteration on clusters
 constexpr int NE = kMaxN / 32;    // eigenvalues per warp in the multisection
 constexpr float kEps32 = 5.9604645e-8f;
@@ -81,8 +84,8 @@ __global__ void __launch_bounds__(LT) level_eig_kernel(LevelArgs a) {
   __shared__ float red[LW];
   __shared__ int cl_start[kMaxN + 1], cl_of[kMaxN], fb[kMaxN];
   __shared__ int s_ncl, s_r, s_b, s_go;
-  __shared__ float s_gl, s_gu, s_pivmin, s_tn, s_nrm2, s_x0, s_lmax_est;
-  __shared__ int s_rcount;
+  __shared__ float s_gl, s_gu, s_pivmin, s_tn, s_lmax_est;
+  __shared__ int s_rcount, s_reflect;
   __shared__ double s_scale;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = a.n;
@@ -128,149 +131,148 @@ __global__ void __launch_bounds__(LT) level_eig_kernel(LevelArgs a) {
     for (int i = lane; i < m; i += 32) A[i + j * LDA] = (float)(Hf[(b + i) + (int64_t)(b + j) * n] * sc);
   __syncthreads();
 
-  // ---- 1. Householder tridiagonalisation; reflector k (v, beta[k]) is kept in
-  //         column k below the diagonal: T = H_{m-3} ... H_0 A H_0 ... H_{m-3}.
-  //         Two block barriers per step: every thread forms the reflector from the
-  //         column norm (computed by warp 0 in the previous step), the matvec
-  //         p = beta A22 v also yields the partial sums of p^T v, and warp 0,
-  //         which updates the next column, sums its squares for the next step.
-  if (warp == 0 && m > 2) {
-    float s = 0.f;
-    for (int i = 2 + lane; i < m; i += 32) s = fmaf(A[i], A[i], s);
-    s = warp_sum(s);
-    if (lane == 0) {
-      s_nrm2 = s;
-      s_x0 = A[1];
-    }
-  }
-  __syncthreads();
-  // The reflector of step k is H = I - 2 u u^T with the unit vector
-  // u = (x - alpha e_1) / ||x - alpha e_1||, so that no intermediate exceeds the
-  // size of the block (1 / ||v||^2 overflows FP32 on near-null columns).  Column k
-  // keeps the unscaled x until the next step, which stores u there.
-  float prev_inv = 1.f, prev_u0 = 0.f;
-  bool prev_reflect = false;
-  for (int k = 0; k < m - 2; ++k) {
-    const int mp = m - k - 1;
-    float* col = A + (k + 1) + k * LDA;
-    if (prev_reflect) {  // store the previous step's unit reflector in its column
-      float* pc = col - 1 - LDA;  // column k - 1 from row k
-      for (int i = tid; i < mp + 1; i += LT) pc[i] = (i == 0) ? prev_u0 : pc[i] * prev_inv;
-    }
-    const float x0 = s_x0, s1 = s_nrm2;
-    const bool reflect = s1 > 0.f && isfinite(s1);
-    float bt = 0.f, alpha = x0, inv = 1.f, u0 = x0;
-    if (reflect) {
-      const float nrm = sqrtf(fmaf(x0, x0, s1));
-      alpha = (x0 >= 0.f) ? -nrm : nrm;
-      const float v0 = x0 - alpha;
-      inv = rsqrtf(fmaf(v0, v0, s1));
-      u0 = v0 * inv;
-      bt = 2.f;
-    }
-    if (reflect) {
-      // acc = A22 u, row i by one of 4 thread groups (4 independent partial sums
-      // each); partial u^T A22 u per warp
-      const int part = tid / kMaxN, i = tid % kMaxN;
-      float pd = 0.f;
-      if (part < 4 && i < mp) {
-        const int j0 = (mp * part) / 4, j1 = (mp * (part + 1)) / 4;
-        const float* Ai = A + (k + 1 + i);
-        float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
-        int j = j0;
-        if (j == 0 && j < j1) {
-          acc0 = Ai[(k + 1) * LDA] * u0;
-          ++j;
-        }
-        for (; j + 3 < j1; j += 4) {
-          acc0 = fmaf(Ai[(k + 1 + j) * LDA], col[j] * inv, acc0);
-          acc1 = fmaf(Ai[(k + 2 + j) * LDA], col[j + 1] * inv, acc1);
-          acc2 = fmaf(Ai[(k + 3 + j) * LDA], col[j + 2] * inv, acc2);
-          acc3 = fmaf(Ai[(k + 4 + j) * LDA], col[j + 3] * inv, acc3);
-        }
-        for (; j < j1; ++j) acc0 = fmaf(Ai[(k + 1 + j) * LDA], col[j] * inv, acc0);
-        const float acc = (acc0 + acc1) + (acc2 + acc3);
-        pv[part * kMaxN + i] = acc;
-        pd = acc * ((i == 0) ? u0 : col[i] * inv);
-      }
-      pd = warp_sum(pd);
-      if (lane == 0) red[warp] = pd;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      d[k] = A[k + k * LDA];
-      e[k] = alpha;
-      beta[k] = bt;
-    }
-    prev_reflect = reflect;
-    prev_inv = inv;
-    prev_u0 = u0;
-    if (reflect) {
-      float uau = 0.f;
-      for (int w = 0; w < LW; ++w) uau += red[w];
-      // p = 2 A22 u, K = u^T p = 2 u^T A22 u, w = p - K u = 2 (acc - uau u)
-      // A22 -= u w^T + w u^T; warp per column, lane per row
-      float vi[NE], wi[NE];
+  // ---- 1. Householder tridiagonalisation with the matrix in registers: thread
+  //         (warp w, lane l) holds rows 12w .. 12w+11 x columns 6l .. 6l+5 (the
+  //         192 x 192 FP32 block fills about half the register file).  Per column k:
+  //           (a) the owners of column k publish rows > k and d[k];
+  //           (b) warp 0 forms the unit reflector u (H = I - 2 u u^T; no
+  //               1 / ||v||^2 intermediate, which overflows FP32 on near-null
+  //               columns) and stores it for the back-transformation;
+  //           (c) p = A u: register FMAs, rows reduced across lanes by
+  //               interleaved shuffles;
+  //           (d) A -= u w^T + w u^T, w = 2 (p - (u^T p) u), in registers.
+  //         Rows and columns <= k are never read again, so (c) and (d) leave them
+  //         unmasked; warps whose rows are all <= k skip both.
+  {
+    float* xcol = pv;               // kMaxN: column k
+    float* uvec = pv + kMaxN;       // kMaxN: reflector
+    float* pvec = pv + 2 * kMaxN;   // kMaxN: p = A u
+    const int r0 = warp * TRR, c0 = lane * TRC;
+    float at[TRR][TRC];
 #pragma unroll
-      for (int q = 0; q < NE; ++q) {
-        const int i = lane + 32 * q;
-        const float v = (i == 0) ? u0 : ((i < mp) ? col[i] * inv : 0.f);
-        vi[q] = v;
-        wi[q] = (i < mp) ? 2.f * fmaf(-uau, v, pv[i] + pv[kMaxN + i] + pv[2 * kMaxN + i] +
-                                                     pv[3 * kMaxN + i])
-                         : 0.f;
+    for (int r = 0; r < TRR; ++r)
+#pragma unroll
+      for (int c = 0; c < TRC; ++c) {
+        const int i = r0 + r, j = c0 + c;
+        at[r][c] = (i < m && j < m) ? A[i + j * LDA] : 0.f;
       }
-      for (int j = warp; j < mp; j += LW) {
-        const float vj = (j == 0) ? u0 : col[j] * inv;
-        const float wj =
-            2.f * fmaf(-uau, vj, pv[j] + pv[kMaxN + j] + pv[2 * kMaxN + j] + pv[3 * kMaxN + j]);
-        float* Aj = A + (k + 1) + (k + 1 + j) * LDA;
+    for (int k = 0; k < m - 2; ++k) {
+      // (a) column k below the diagonal, and d[k]
+      if (lane == k / TRC) {
+#pragma unroll
+        for (int c = 0; c < TRC; ++c)
+          if (c0 + c == k) {
+#pragma unroll
+            for (int r = 0; r < TRR; ++r) {
+              const int i = r0 + r;
+              if (i >= k && i < m) {
+                if (i == k) d[k] = at[r][c];
+                else xcol[i] = at[r][c];
+              }
+            }
+          }
+      }
+      __syncthreads();
+      // (b) reflector from xcol[k+1 .. m-1]
+      if (warp == 0) {
         float sq = 0.f;
-#pragma unroll
-        for (int q = 0; q < NE; ++q) {
-          const int i = lane + 32 * q;
-          if (i < mp) {
-            const float a = fmaf(-vi[q], wj, fmaf(-wi[q], vj, Aj[i]));
-            Aj[i] = a;
-            if (i >= 2) sq = fmaf(a, a, sq);  // next column below its subdiagonal
-          }
+        for (int i = k + 2 + lane; i < m; i += 32) sq = fmaf(xcol[i], xcol[i], sq);
+        sq = warp_sum(sq);
+        const float x0 = xcol[k + 1];
+        const bool refl = sq > 0.f && isfinite(sq);
+        float alpha = x0, inv = 0.f, v0 = 0.f;
+        if (refl) {
+          const float nrm = sqrtf(fmaf(x0, x0, sq));
+          alpha = (x0 >= 0.f) ? -nrm : nrm;
+          v0 = x0 - alpha;
+          inv = rsqrtf(fmaf(v0, v0, sq));
         }
-        if (j == 0) {  // column k + 1: norm for the next step
-          sq = warp_sum(sq);
-          __syncwarp();  // lane 1's update of Aj[1] is visible to lane 0
-          if (lane == 0) {
-            s_nrm2 = sq;
-            s_x0 = Aj[1];
-          }
+        for (int i = lane; i < kMaxN; i += 32) {
+          const float ui = (!refl || i <= k || i >= m) ? 0.f : (i == k + 1) ? v0 * inv : xcol[i] * inv;
+          uvec[i] = ui;
+          if (i > k && i < m) a.V[i + (int64_t)k * ldz] = ui;
+        }
+        if (lane == 0) {
+          e[k] = alpha;
+          beta[k] = refl ? 2.f : 0.f;
+          a.vb[k] = refl ? 2.f : 0.f;
+          s_reflect = refl ? 1 : 0;
         }
       }
-    } else if (warp == 0 && k + 1 < m - 2) {
-      // no reflection: column k + 1 is unchanged; its norm for the next step
-      const float* Aj = A + (k + 1) + (k + 1) * LDA;
-      float sq = 0.f;
-      for (int i = 2 + lane; i < mp; i += 32) sq = fmaf(Aj[i], Aj[i], sq);
-      sq = warp_sum(sq);
-      if (lane == 0) {
-        s_nrm2 = sq;
-        s_x0 = Aj[1];
+      __syncthreads();
+      if (!s_reflect) continue;  // uniform: column already reduced
+      const bool live = r0 + TRR - 1 > k;  // warp has rows in the trailing block
+      // (c) p = A u
+      {
+        float acc[TRR];
+        if (live) {
+          float uc[TRC];
+#pragma unroll
+          for (int c = 0; c < TRC; ++c) uc[c] = uvec[c0 + c];
+#pragma unroll
+          for (int r = 0; r < TRR; ++r) {
+            float t = 0.f;
+#pragma unroll
+            for (int c = 0; c < TRC; ++c) t = fmaf(at[r][c], uc[c], t);
+            acc[r] = t;
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int r = 0; r < TRR; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+        } else {
+#pragma unroll
+          for (int r = 0; r < TRR; ++r) acc[r] = 0.f;
+        }
+        // lane r < TRR publishes row r (spreads the stores over the warp)
+        float up = 0.f;
+#pragma unroll
+        for (int r = 0; r < TRR; ++r)
+          if (lane == r) {
+            pvec[r0 + r] = acc[r];
+            up = acc[r] * uvec[r0 + r];
+          }
+        up = warp_sum(up);
+        if (lane == 0) red[warp] = up;
+      }
+      __syncthreads();
+      // (d) rank-2 update in registers
+      if (live) {
+        const float uau = warp_sum(lane < LW ? red[lane] : 0.f);
+        float ur[TRR], wr[TRR], ucv[TRC], wc[TRC];
+#pragma unroll
+        for (int r = 0; r < TRR; ++r) {
+          ur[r] = uvec[r0 + r];
+          wr[r] = 2.f * fmaf(-uau, ur[r], pvec[r0 + r]);
+        }
+#pragma unroll
+        for (int c = 0; c < TRC; ++c) {
+          ucv[c] = uvec[c0 + c];
+          wc[c] = 2.f * fmaf(-uau, ucv[c], pvec[c0 + c]);
+        }
+#pragma unroll
+        for (int r = 0; r < TRR; ++r)
+#pragma unroll
+          for (int c = 0; c < TRC; ++c) at[r][c] = fmaf(-ur[r], wc[c], fmaf(-wr[r], ucv[c], at[r][c]));
       }
     }
-    __syncthreads();
-  }
-  if (prev_reflect && m > 2) {  // the last step's unit reflector (column m - 3)
-    float* pc = A + (m - 2) + (m - 3) * LDA;
-    for (int i = tid; i < 2; i += LT) pc[i] = (i == 0) ? prev_u0 : pc[i] * prev_inv;
+    // the trailing 2 x 2 block
+#pragma unroll
+    for (int r = 0; r < TRR; ++r)
+#pragma unroll
+      for (int c = 0; c < TRC; ++c) {
+        const int i = r0 + r, j = c0 + c;
+        if (m >= 2 && i == m - 2 && j == m - 2) d[m - 2] = at[r][c];
+        if (m >= 2 && i == m - 1 && j == m - 2) e[m - 2] = at[r][c];
+        if (i == m - 1 && j == m - 1) d[m - 1] = at[r][c];
+      }
   }
   __syncthreads();
   if (tid == 0) {
-    if (m >= 2) {
-      d[m - 2] = A[(m - 2) + (m - 2) * LDA];
-      e[m - 2] = A[(m - 1) + (m - 2) * LDA];
-      beta[m - 2] = 0.f;
-    }
-    d[m - 1] = A[(m - 1) + (m - 1) * LDA];
+    if (m >= 2) beta[m - 2] = 0.f;
     beta[m - 1] = 0.f;
     e[m - 1] = 0.f;
+    for (int k = max(m - 2, 0); k < m; ++k) a.vb[k] = 0.f;
     float gl = INFINITY, gu = -INFINITY, emax2 = 0.f;
     for (int i = 0; i < m; ++i) {
       const float r = (i > 0 ? fabsf(e[i - 1]) : 0.f) + (i < m - 1 ? fabsf(e[i]) : 0.f);
@@ -287,49 +289,43 @@ __global__ void __launch_bounds__(LT) level_eig_kernel(LevelArgs a) {
   }
   __syncthreads();
 
-  // reflectors to global memory (the back-transformation runs on all SMs)
-  for (int k = warp; k < m; k += LW)
-    for (int i = lane; i < m; i += 32) a.V[i + (int64_t)k * ldz] = (k < m - 2 && i > k) ? A[i + k * LDA] : 0.f;
-  for (int k = tid; k < m; k += LT) a.vb[k] = beta[k];
-  __syncthreads();
-
   // ---- 2. eigenvalues (descending) by multisection: a group of 8 lanes tests 8
   //         shifts per eigenvalue and round (9 subintervals); each thread carries
-  //         two eigenvalues (groups g and g + 128).  Three rounds for all
+  //         NB3 eigenvalues (g, g + 64, g + 128).  Three rounds for all
   //         eigenvalues, then the number resolved (lambda >= tau * lambda_max) by
   //         one exact Sturm count, then five more rounds for the resolved ones and
   //         a margin of 8 (the rest only seed estimates for the next level).
   {
     const int grp = tid >> 3, gl8 = tid & 7;
-    float lo[2], hi[2];
-    int qidx[2];
+    float lo[NB3], hi[NB3];
+    int qidx[NB3];
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < NB3; ++t) {
       lo[t] = s_gl;
       hi[t] = s_gu;
-      const int jj = grp + 128 * t;
+      const int jj = grp + (LT / 8) * t;
       qidx[t] = (jj < m) ? m - 1 - jj : 0;  // ascending index
     }
     const float pivmin = s_pivmin;
     const bool fin = isfinite(s_gl) && isfinite(s_gu);
     auto rounds = [&](int nr, int jlimit) {
       for (int round = 0; round < nr; ++round) {
-        float x[2], q[2];
-        int cnt[2];
-        bool act[2];
+        float x[NB3], q[NB3];
+        int cnt[NB3];
+        bool act[NB3];
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
-          act[t] = fin && (grp + 128 * t) < jlimit;
+        for (int t = 0; t < NB3; ++t) {
+          act[t] = fin && (grp + (LT / 8) * t) < jlimit;
           x[t] = lo[t] + (hi[t] - lo[t]) * (float)(gl8 + 1) * (1.f / 9.f);
           q[t] = d[0] - x[t];
           if (fabsf(q[t]) < pivmin) q[t] = -pivmin;
           cnt[t] = q[t] < 0.f;
         }
-        if (act[0] || act[1]) {
+        if (act[0] || act[1] || act[2]) {
           for (int i = 1; i < m; ++i) {
             const float di = d[i], ei = e2[i - 1];
 #pragma unroll
-            for (int t = 0; t < 2; ++t) {
+            for (int t = 0; t < NB3; ++t) {
               q[t] = (di - x[t]) - __fdividef(ei, q[t]);
               if (fabsf(q[t]) < pivmin) q[t] = -pivmin;
               cnt[t] += q[t] < 0.f;
@@ -337,7 +333,7 @@ __global__ void __launch_bounds__(LT) level_eig_kernel(LevelArgs a) {
           }
         }
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
+        for (int t = 0; t < NB3; ++t) {
           const unsigned bal = __ballot_sync(0xffffffffu, cnt[t] <= qidx[t]);
           const int nle = __popc((bal >> (lane & 24)) & 0xffu);
           const float span = hi[t] - lo[t];
@@ -375,8 +371,8 @@ __global__ void __launch_bounds__(LT) level_eig_kernel(LevelArgs a) {
     rounds(5, min(m, s_rcount + 8));
     if (gl8 == 0) {
 #pragma unroll
-      for (int t = 0; t < 2; ++t) {
-        const int jj = grp + 128 * t;
+      for (int t = 0; t < NB3; ++t) {
+        const int jj = grp + (LT / 8) * t;
         if (jj < m) lamf[jj] = 0.5f * (lo[t] + hi[t]);
       }
     }
