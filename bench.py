@@ -52,11 +52,6 @@ def set_grid(ny: int, nx: int):
         WORKLOAD = WORKLOAD.replace("M=2^23 (2048x4096 grid)", f"M={M_FULL} ({ny}x{nx} grid)")
 
 
-def _dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
 
 
 def _peaks():
@@ -118,11 +113,12 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def make_batches(device, count: int):
+def make_batches(device, count: int, rank: int = 0):
     import torch
 
-    from paper_2108_08845_gb300 import synthetic
-    gen = synthetic.TravellingWaves(NY, NX, NMODES, DECAY, NOISE, SEED, corr_len=CORR,
+    from paper_2108_08845_gb300 import replicas, synthetic
+    gen = synthetic.TravellingWaves(NY, NX, NMODES, DECAY, NOISE, replicas.stream_seed(SEED, rank),
+                                    corr_len=CORR,
                                     device=device, dtype=torch.float32)
     out = []
     for i in range(count):
@@ -243,7 +239,8 @@ def cpu_sample(updates: int = 2, ny: int = 128, nx: int = 256):
 
 
 def reference_main(args):
-    ws, rank, _ = _dist()
+    from paper_2108_08845_gb300 import replicas
+    ws, rank, _ = replicas.world()
     if rank != 0:
         return 0
     samples = []
@@ -289,7 +286,8 @@ def main():
     import torch
 
     from paper_2108_08845_gb300 import psvd
-    ws, rank, local = _dist()
+    from paper_2108_08845_gb300 import replicas
+    ws, rank, local = replicas.world()
     torch.cuda.set_device(local)
     if ws > 1:
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -299,7 +297,7 @@ def main():
     arms = {"both": ["bf16_tc", "fp32"], "fp32": ["fp32"], "bf16_tc": ["bf16_tc"]}[args.precision]
     prec_code = {"fp32": psvd.PSVD_PREC_FP32, "bf16_tc": psvd.PSVD_PREC_BF16_TC}
     nb = min(32, 1 + args.warmup + args.steps)
-    batches = make_batches("cuda", nb)
+    batches = make_batches("cuda", nb, rank)
     results = {}
     for arm in arms:
         sampler = ClockSampler(local) if rank == 0 else None
@@ -312,20 +310,13 @@ def main():
             results[arm] = None  # the tensor-core path is not available in this build
     head = next(a for a in arms if results.get(a))
     r = results[head]
-    ms_local = r["ms"]
-    if ws > 1:
-        t = torch.tensor([ms_local], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_max = float(t.item())
-    else:
-        ms_max = ms_local
-    value = ws * args.steps * BATCH / (ms_max * 1e-3)
     e2e = (run_e2e(psvd, batches, prec_code[head], args.e2e_steps, stream) if args.e2e_steps > 0
            else None)
-    if ws > 1 and e2e:
-        t = torch.tensor([e2e["value"]], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MIN)
-        e2e["value"] = float(t.item()) * ws
+    ms_max, e2e_min = replicas.reduce_timing(r["ms"], e2e["value"] if e2e else None, ws,
+                                             device="cuda")
+    value = replicas.job_throughput(ws, args.steps, BATCH, ms_max)
+    if e2e:
+        e2e["value"] = e2e_min * ws
     if rank == 0:
         rf, avg = roofline(r, head, hbm_peak, peak_kind)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
