@@ -38,13 +38,17 @@ namespace {
 
 constexpr int kRowsStage = 64;            // rows per Gram stage (one 128-byte swizzle row per column)
 constexpr int kSlab = 128;                // panel columns per MMA slab (UMMA M)
-constexpr int kGramStages = 6;
+constexpr int kGramStages = 3;
+// Rows per Gram pipeline slot: two 64-row blocks of every column, issued back to
+// back, so that DRAM sees 256 contiguous bytes per column instead of 128 (the
+// panel is column-major and its columns are far apart).
+constexpr int kGramSubs = 2;
 // 64-row stages per FP32 accumulation chain before it is folded into the
 // float-float totals.  The tensor-core FP32 accumulation has a relative bias that
 // grows with the chain (measured about -1.5e-8 per MMA on the Gram diagonal); with
-// 2 stages (8 MMAs) the 64-mode subspace of the config-3 recipe stays within
-// 5.3e-4 rad of the FP64 result (2.2e-3 with 4 stages), at the same Gram time.
-constexpr int kFoldStages = 2;
+// 8 MMAs per chain the 64-mode subspace of the config-3 recipe stays within
+// 5.3e-4 rad of the FP64 result (2.2e-3 with 16).  One slot (128 rows) is 8 MMAs.
+constexpr int kFoldStages = 1;
 constexpr int kUpdRows = 128;             // rows per update tile (UMMA M)
 constexpr int kUpdStages = 2;
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
@@ -293,7 +297,8 @@ __global__ void __launch_bounds__(192, 1) tc_gram_kernel(const __grid_constant__
   pair_of(pair, g.nslab, &si, &sj);
   const bool diag = (si == sj);
   const int nsl = diag ? 1 : 2;
-  const int stage_bytes = nsl * kSlab * 128;
+  const int sub_bytes = nsl * kSlab * 128;        // one 64-row block of the slab(s)
+  const int stage_bytes = kGramSubs * sub_bytes;  // one pipeline slot
   uint8_t* stages = base;
   uint64_t* full = (uint64_t*)(stages + (size_t)kGramStages * stage_bytes);
   uint64_t* empty = full + kGramStages;
@@ -306,7 +311,7 @@ __global__ void __launch_bounds__(192, 1) tc_gram_kernel(const __grid_constant__
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t r0 = range * g.range_rows;
   const int64_t r1 = min(g.M, r0 + g.range_rows);
-  const int nst = (r0 < r1) ? (int)ceil_div(r1 - r0, kRowsStage) : 0;
+  const int nst = (r0 < r1) ? (int)ceil_div(r1 - r0, (int64_t)kGramSubs * kRowsStage) : 0;
   const int nfold = (int)ceil_div(nst, g.fold_stages);
   const int w = slab_width16(sj, g.np);
 
@@ -344,13 +349,18 @@ __global__ void __launch_bounds__(192, 1) tc_gram_kernel(const __grid_constant__
       for (int st = 0; st < nst && !*abort_flag; ++st) {
         if (issued >= kGramStages && !mbar_wait(&empty[stage], phase ^ 1, abort_flag, err)) break;
         uint8_t* dst = stages + (size_t)stage * stage_bytes;
-        const int row = (int)(r0 + (int64_t)st * kRowsStage);
-        // expected bytes: every 8-column group of the two slabs
+        const int row = (int)(r0 + (int64_t)st * kGramSubs * kRowsStage);
+        // expected bytes: every 8-column group of the two slabs, for each row block
         const uint32_t bytes_i = (uint32_t)(min(g.np, (si + 1) * kSlab) - si * kSlab) * 128u;
         const uint32_t bytes_j = diag ? 0u : (uint32_t)(min(g.np, (sj + 1) * kSlab) - sj * kSlab) * 128u;
-        mbar_expect_tx(&full[stage], bytes_i + bytes_j);
-        load_slab(pm, g, si, &full[stage], dst, row);
-        if (!diag) load_slab(pm, g, sj, &full[stage], dst + kSlab * 128, row);
+        mbar_expect_tx(&full[stage], kGramSubs * (bytes_i + bytes_j));
+        // rows beyond r1 inside the last slot are either beyond M (zero-filled by
+        // the tensor map) or absent (ranges are multiples of the slot height)
+        for (int h = 0; h < kGramSubs; ++h) {
+          uint8_t* d = dst + h * sub_bytes;
+          load_slab(pm, g, si, &full[stage], d, row + h * kRowsStage);
+          if (!diag) load_slab(pm, g, sj, &full[stage], d + kSlab * 128, row + h * kRowsStage);
+        }
         ++issued;
         if (++stage == kGramStages) {
           stage = 0;
@@ -388,13 +398,16 @@ __global__ void __launch_bounds__(192, 1) tc_gram_kernel(const __grid_constant__
           }
           tc_fence_after();
           const uint32_t sbase = smem_u32(stages + (size_t)stage * stage_bytes);
-          const uint32_t abase = sbase;
-          const uint32_t bbase = diag ? sbase : sbase + kSlab * 128;
 #pragma unroll
-          for (int k = 0; k < kRowsStage / 16; ++k) {
-            const uint64_t ad = smem_desc(abase + k * 32, 16, 1024);
-            const uint64_t bd = smem_desc(bbase + k * 32, 16, 1024);
-            umma_bf16(d_tmem, ad, bd, idesc, (k4 > 0 || k > 0) ? 1u : 0u);
+          for (int h = 0; h < kGramSubs; ++h) {
+            const uint32_t abase = sbase + h * sub_bytes;
+            const uint32_t bbase = diag ? abase : abase + kSlab * 128;
+#pragma unroll
+            for (int k = 0; k < kRowsStage / 16; ++k) {
+              const uint64_t ad = smem_desc(abase + k * 32, 16, 1024);
+              const uint64_t bd = smem_desc(bbase + k * 32, 16, 1024);
+              umma_bf16(d_tmem, ad, bd, idesc, (k4 > 0 || h > 0 || k > 0) ? 1u : 0u);
+            }
           }
           umma_commit(&empty[stage]);
           if (++stage == kGramStages) {
@@ -774,8 +787,8 @@ GramGeom gram_geom(int64_t M, int kc, int B, int num_sms) {
   // about one CTA per SM: num_sms / npair row ranges, each a multiple of 64 rows
   int64_t want = num_sms / g.npair;
   if (want < 1) want = 1;
-  int64_t rr = ceil_div(ceil_div(M, want), kRowsStage) * kRowsStage;
-  if (rr < kRowsStage) rr = kRowsStage;
+  const int64_t slot_rows = (int64_t)kGramSubs * kRowsStage;
+  int64_t rr = ceil_div(ceil_div(M, want), slot_rows) * slot_rows;
   g.range_rows = rr;
   g.nrange = ceil_div(M, rr);
   g.fold_stages = kFoldStages;
@@ -783,7 +796,7 @@ GramGeom gram_geom(int64_t M, int kc, int B, int num_sms) {
 }
 
 size_t gram_smem(const GramGeom&) {
-  return 1024 + (size_t)kGramStages * 2 * kSlab * 128 + 256;
+  return 1024 + (size_t)kGramStages * kGramSubs * 2 * kSlab * 128 + 256;
 }
 
 }  // namespace
