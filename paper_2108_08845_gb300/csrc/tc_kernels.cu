@@ -8,13 +8,15 @@
 // cores is exact; accumulation is FP32 in tensor memory (TMEM).
 //
 // tc_gram_kernel: the panel Gram P'^T P' (step 1's R^T R).  P' is streamed in
-//   64-row stages by TMA (SWIZZLE_128B, each column one 128-byte row, i.e. the
-//   K-major canonical layout with K = rows).  Each CTA owns one pair of
-//   128-column slabs (i <= j) over one row range and issues one tcgen05.mma per
-//   16 rows into an FP32 TMEM accumulator; every 128 rows the epilogue folds
-//   that accumulator into a float-float (hi, lo) sum held in TMEM (TwoSum), so
-//   FP32 rounding only acts on 8-MMA chains.  The range blocks are summed in
-//   FP64 in a fixed order and Uh/Ul are folded back into U on the small side.
+//   128-row slots by TMA (SWIZZLE_128B, each column's 64-row block one 128-byte
+//   row, i.e. the K-major canonical layout with K = rows).  A cluster of CTAs, one
+//   per 128 x 128 block (pair of 128-column slabs i <= j), takes every nrange-th
+//   slot; each slab is read once and multicast to the CTAs whose blocks use it.
+//   Each CTA issues one tcgen05.mma per 16 rows into an FP32 TMEM accumulator;
+//   after every slot the epilogue folds that accumulator into a float-float sum
+//   held in TMEM (Fast2Sum), so FP32 rounding only acts on 8-MMA chains.  The
+//   cluster blocks are summed in FP64 in a fixed order and Uh/Ul are folded back
+//   into U on the small side.
 // tc_update_kernel: step 4, U_new = [U | A] T.  T (n x k1, FP32) is split
 //   exactly into three BF16 parts, so one MMA with N = 3 * k1p computes the
 //   three partial products; P' row tiles of 128 rows are the MN-major A operand
@@ -46,8 +48,9 @@ constexpr int kGramSubs = 2;
 // 64-row stages per FP32 accumulation chain before it is folded into the
 // float-float totals.  The tensor-core FP32 accumulation has a relative bias that
 // grows with the chain (measured about -1.5e-8 per MMA on the Gram diagonal); with
-// 8 MMAs per chain the 64-mode subspace of the config-3 recipe stays within
-// 5.3e-4 rad of the FP64 result (2.2e-3 with 16).  One slot (128 rows) is 8 MMAs.
+// 8 MMAs per chain the 64-mode subspace of the 256-mode travelling-wave recipe
+// (K = 64, B = 128) stays within 5.3e-4 rad of the FP64 result (2.2e-3 with 16).
+// One slot (128 rows) is 8 MMAs.
 constexpr int kFoldStages = 1;
 constexpr int kUpdRows = 128;             // rows per update tile (UMMA M)
 constexpr int kUpdStages = 2;
@@ -107,6 +110,26 @@ __device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* ba
       "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
       : "memory");
 }
+// As tma_load_2d, delivered to the same shared-memory offset (data and barrier
+// bytes) in every CTA of the cluster named in mask.
+__device__ __forceinline__ void tma_load_2d_mc(const CUtensorMap* map, uint64_t* bar, void* dst,
+                                               int x, int y, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// All threads of every CTA of the cluster (a CTA launched without a cluster is one).
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                    smem_u32(dst)),
@@ -136,6 +159,15 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(bar))
+      : "memory");
+}
+// Arrives (once the issued MMAs complete) on the mbarrier at this offset in every
+// CTA of the cluster named in mask.
+__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
       : "memory");
 }
 // 32 consecutive TMEM columns of this thread's lane, without waiting.
@@ -195,13 +227,15 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const float* v) {
       : "memory");
 }
 
-// Knuth TwoSum: hi + lo accumulates x with the rounding error of hi + x kept in lo.
-__device__ __forceinline__ void two_sum_fold(float& hi, float& lo, float x) {
+// Fast2Sum fold (Dekker): hi + lo accumulates x, lo collecting the rounding error of
+// hi + x.  The error term is exact when |hi| >= |x|, which holds for a running Gram
+// total once its first chains are in (one 128-row chain is small next to the sum);
+// otherwise at most one rounding of the sum is lost.
+__device__ __forceinline__ void fold(float& hi, float& lo, float x) {
   const float s = __fadd_rn(hi, x);
-  const float bp = __fsub_rn(s, hi);
-  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+  const float z = __fsub_rn(s, hi);
+  lo = __fadd_rn(lo, __fsub_rn(x, z));
   hi = s;
-  lo = __fadd_rn(lo, err);
 }
 
 // Shared-memory matrix descriptor, SWIZZLE_128B (layout type 2), version 1.
@@ -235,8 +269,8 @@ struct GramGeom {
   int np;      // 2*kcp + Bp
   int nslab;   // ceil(np / 128)
   int npair;   // nslab*(nslab+1)/2
-  int64_t range_rows;  // rows per CTA range (multiple of 64)
-  int64_t nrange;
+  int64_t nslot;       // 128-row slots covering M
+  int64_t nrange;      // clusters; cluster r takes slots r, r + nrange, ...
   int fold_stages;     // 64-row stages (4 MMAs each) per FP32 accumulation chain
 };
 
@@ -263,9 +297,9 @@ __device__ __forceinline__ int slab_width16(int s, int np) {
 
 // Loads slab s (padded-panel columns [128 s, 128 s + 128)) for rows [row, row + 64)
 // into dst: each plane's column range inside the slab is tiled by boxes of 64,
-// 32, 16 and 8 columns.
+// 32, 16 and 8 columns.  mask != 0: multicast to those CTAs of the cluster.
 __device__ __forceinline__ void load_slab(const PanelMaps& pm, const GramGeom& g, int s,
-                                          uint64_t* bar, uint8_t* dst, int row) {
+                                          uint64_t* bar, uint8_t* dst, int row, uint16_t mask) {
   const int lo = s * kSlab, hi = min(g.np, (s + 1) * kSlab);
   const int start[3] = {0, g.kcp, 2 * g.kcp};
   const int end[3] = {g.kcp, 2 * g.kcp, g.np};
@@ -275,29 +309,39 @@ __device__ __forceinline__ void load_slab(const PanelMaps& pm, const GramGeom& g
     while (c < c_end) {
       const int left = c_end - c;
       const int wi = left >= 64 ? 0 : left >= 32 ? 1 : left >= 16 ? 2 : 3;
-      tma_load_2d(&pm.m[src][wi], bar, dst + (c - lo) * 128, row, c - start[src]);
+      if (mask)
+        tma_load_2d_mc(&pm.m[src][wi], bar, dst + (c - lo) * 128, row, c - start[src], mask);
+      else
+        tma_load_2d(&pm.m[src][wi], bar, dst + (c - lo) * 128, row, c - start[src]);
       c += 64 >> wi;
     }
   }
 }
 
-// One CTA = one 128 x 128 block (slab pair) of the Gram over one row range.
+// One CTA = one 128 x 128 block (slab pair si <= sj) of the Gram over the slots of
+// its cluster.  The cluster has one CTA per block (rank = pair index); all CTAs
+// use the same stage layout, per 64-row block [slab 0 | slab 1], so a slab lands
+// at the same offset in every CTA that uses it.  The 64-row blocks of a slab are
+// split between its users: each issues its share as TMA loads multicast to all of
+// them (slab 0 to the (0,0) and (0,1) CTAs, slab 1 to the (0,1) and (1,1) CTAs).
+// A CTA's full barrier expects all bytes it receives; its empty barrier collects
+// the MMA commits of every CTA of the cluster, so no CTA's copy lands in a stage
+// that another CTA still reads.
 // TMEM: two FP32 accumulators (columns 0 and 128) alternate between the MMA warp
 // and the epilogue, which folds each finished 128-row partial into a float-float
-// running sum (hi at column 256, lo at 384).  The range's block is written as
-// FP64 (hi + lo) to partial[range][pair][128][128].
+// running sum (hi at column 256, lo at 384).  The block is written as FP64
+// (hi + lo) to partial[range][pair][128][128].
 __global__ void __launch_bounds__(192, 1) tc_gram_kernel(const __grid_constant__ PanelMaps pm,
                                                          GramGeom g, double* __restrict__ partial,
                                                          int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const int pair = blockIdx.x % g.npair;
+  const int pair = g.npair > 1 ? (int)cluster_rank() : 0;
   const int64_t range = blockIdx.x / g.npair;
   int si, sj;
   pair_of(pair, g.nslab, &si, &sj);
   const bool diag = (si == sj);
-  const int nsl = diag ? 1 : 2;
-  const int sub_bytes = nsl * kSlab * 128;        // one 64-row block of the slab(s)
+  const int sub_bytes = g.nslab * kSlab * 128;    // one 64-row block of every slab
   const int stage_bytes = kGramSubs * sub_bytes;  // one pipeline slot
   uint8_t* stages = base;
   uint64_t* full = (uint64_t*)(stages + (size_t)kGramStages * stage_bytes);
@@ -309,9 +353,7 @@ __global__ void __launch_bounds__(192, 1) tc_gram_kernel(const __grid_constant__
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t r0 = range * g.range_rows;
-  const int64_t r1 = min(g.M, r0 + g.range_rows);
-  const int nst = (r0 < r1) ? (int)ceil_div(r1 - r0, (int64_t)kGramSubs * kRowsStage) : 0;
+  const int nst = range < g.nslot ? (int)((g.nslot - 1 - range) / g.nrange + 1) : 0;
   const int nfold = (int)ceil_div(nst, g.fold_stages);
   const int w = slab_width16(sj, g.np);
 
@@ -321,7 +363,7 @@ __global__ void __launch_bounds__(192, 1) tc_gram_kernel(const __grid_constant__
   if (threadIdx.x == 0) {
     for (int s = 0; s < kGramStages; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], g.npair);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
@@ -338,28 +380,39 @@ __global__ void __launch_bounds__(192, 1) tc_gram_kernel(const __grid_constant__
   }
   tc_fence_before();
   __syncthreads();
+  cluster_sync_all();  // every CTA's barriers exist before any multicast or commit reaches them
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
   if (warp == 0) {
     if (lane == 0) {
       // ---------------------------------------------------------- TMA producer
+      // bytes of one 64-row block of slab s; this CTA receives both blocks of
+      // slab si and of slab sj
+      uint32_t bytes_s[2];
+      for (int s = 0; s < 2; ++s)
+        bytes_s[s] = s < g.nslab ? (uint32_t)(min(g.np, (s + 1) * kSlab) - s * kSlab) * 128u : 0u;
+      const uint32_t expect = kGramSubs * (bytes_s[si] + (diag ? 0u : bytes_s[sj]));
       int stage = 0, issued = 0;
       uint32_t phase = 0;
       for (int st = 0; st < nst && !*abort_flag; ++st) {
         if (issued >= kGramStages && !mbar_wait(&empty[stage], phase ^ 1, abort_flag, err)) break;
         uint8_t* dst = stages + (size_t)stage * stage_bytes;
-        const int row = (int)(r0 + (int64_t)st * kGramSubs * kRowsStage);
-        // expected bytes: every 8-column group of the two slabs, for each row block
-        const uint32_t bytes_i = (uint32_t)(min(g.np, (si + 1) * kSlab) - si * kSlab) * 128u;
-        const uint32_t bytes_j = diag ? 0u : (uint32_t)(min(g.np, (sj + 1) * kSlab) - sj * kSlab) * 128u;
-        mbar_expect_tx(&full[stage], kGramSubs * (bytes_i + bytes_j));
-        // rows beyond r1 inside the last slot are either beyond M (zero-filled by
-        // the tensor map) or absent (ranges are multiples of the slot height)
+        const int row = (int)((range + (int64_t)st * g.nrange) * (kGramSubs * kRowsStage));
+        mbar_expect_tx(&full[stage], expect);
+        // rows of the last slot beyond M are zero-filled by the tensor map
         for (int h = 0; h < kGramSubs; ++h) {
           uint8_t* d = dst + h * sub_bytes;
-          load_slab(pm, g, si, &full[stage], d, row + h * kRowsStage);
-          if (!diag) load_slab(pm, g, sj, &full[stage], d + kSlab * 128, row + h * kRowsStage);
+          if (g.npair == 1) {
+            load_slab(pm, g, 0, &full[stage], d, row + h * kRowsStage, 0);
+          } else {
+            // block h of slab 0: CTA h (h = 0: (0,0), h = 1: (0,1)); of slab 1:
+            // CTA 2 - h (h = 0: (1,1), h = 1: (0,1))
+            if (pair == h)
+              load_slab(pm, g, 0, &full[stage], d, row + h * kRowsStage, (uint16_t)0x3);
+            if (pair == 2 - h)
+              load_slab(pm, g, 1, &full[stage], d + kSlab * 128, row + h * kRowsStage, (uint16_t)0x6);
+          }
         }
         ++issued;
         if (++stage == kGramStages) {
@@ -382,6 +435,7 @@ __global__ void __launch_bounds__(192, 1) tc_gram_kernel(const __grid_constant__
     if (lane == 0) {
       // --------------------------------------------------------- MMA issuer
       const uint32_t idesc = idesc_bf16(w, 0, 0);
+      const uint16_t all = (uint16_t)((1u << g.npair) - 1u);
       int stage = 0;
       uint32_t phase = 0;
       int st = 0;
@@ -400,8 +454,8 @@ __global__ void __launch_bounds__(192, 1) tc_gram_kernel(const __grid_constant__
           const uint32_t sbase = smem_u32(stages + (size_t)stage * stage_bytes);
 #pragma unroll
           for (int h = 0; h < kGramSubs; ++h) {
-            const uint32_t abase = sbase + h * sub_bytes;
-            const uint32_t bbase = diag ? abase : abase + kSlab * 128;
+            const uint32_t abase = sbase + h * sub_bytes + si * kSlab * 128;
+            const uint32_t bbase = sbase + h * sub_bytes + sj * kSlab * 128;
 #pragma unroll
             for (int k = 0; k < kRowsStage / 16; ++k) {
               const uint64_t ad = smem_desc(abase + k * 32, 16, 1024);
@@ -409,7 +463,10 @@ __global__ void __launch_bounds__(192, 1) tc_gram_kernel(const __grid_constant__
               umma_bf16(d_tmem, ad, bd, idesc, (k4 > 0 || h > 0 || k > 0) ? 1u : 0u);
             }
           }
-          umma_commit(&empty[stage]);
+          if (g.npair > 1)
+            umma_commit_mc(&empty[stage], all);
+          else
+            umma_commit(&empty[stage]);
           if (++stage == kGramStages) {
             stage = 0;
             phase ^= 1;
@@ -457,7 +514,7 @@ __global__ void __launch_bounds__(192, 1) tc_gram_kernel(const __grid_constant__
           for (int i = 0; i < 32; ++i) {
             fh[i] = __uint_as_float(h[i]);
             fl[i] = __uint_as_float(l[i]);
-            two_sum_fold(fh[i], fl[i], __uint_as_float(a[i]));
+            fold(fh[i], fl[i], __uint_as_float(a[i]));
           }
         }
         tmem_st32(t_hi + c0, fh);
@@ -481,11 +538,12 @@ __global__ void __launch_bounds__(192, 1) tc_gram_kernel(const __grid_constant__
   }
   tc_fence_before();
   __syncthreads();
+  cluster_sync_all();  // no CTA leaves while the cluster may still copy into it or commit to it
   tc_fence_after();
   if (warp == 1) tmem_dealloc(tmem_base, 512);
 }
 
-// Ssum[pair][x][y] = sum over row ranges of the FP64 range blocks, in a fixed order.
+// Ssum[pair][x][y] = sum over the clusters of the FP64 blocks, in a fixed order.
 __global__ void tc_gram_sum_kernel(const double* __restrict__ partial, int64_t nrange, int npair,
                                    double* __restrict__ Ssum) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -776,7 +834,7 @@ bool make_map(CUtensorMap* m, const void* ptr, int64_t rows, int64_t cols, int64
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-GramGeom gram_geom(int64_t M, int kc, int B, int num_sms) {
+GramGeom gram_geom(int64_t M, int kc, int B, int max_clusters) {
   GramGeom g;
   g.M = M;
   g.kcp = (kc + 7) & ~7;
@@ -784,19 +842,45 @@ GramGeom gram_geom(int64_t M, int kc, int B, int num_sms) {
   g.np = 2 * g.kcp + g.Bp;
   g.nslab = (int)ceil_div(g.np, kSlab);
   g.npair = g.nslab * (g.nslab + 1) / 2;
-  // about one CTA per SM: num_sms / npair row ranges, each a multiple of 64 rows
-  int64_t want = num_sms / g.npair;
-  if (want < 1) want = 1;
-  const int64_t slot_rows = (int64_t)kGramSubs * kRowsStage;
-  int64_t rr = ceil_div(ceil_div(M, want), slot_rows) * slot_rows;
-  g.range_rows = rr;
-  g.nrange = ceil_div(M, rr);
+  // every cluster resident at once; the clusters interleave slot by slot, so that
+  // the CTAs in flight read neighbouring rows of every column
+  g.nslot = ceil_div(M, (int64_t)kGramSubs * kRowsStage);
+  int64_t want = max_clusters;
+  if (want > g.nslot) want = g.nslot;
+  g.nrange = want < 1 ? 1 : want;
   g.fold_stages = kFoldStages;
   return g;
 }
 
-size_t gram_smem(const GramGeom&) {
-  return 1024 + (size_t)kGramStages * kGramSubs * 2 * kSlab * 128 + 256;
+size_t gram_smem() { return 1024 + (size_t)kGramStages * kGramSubs * 2 * kSlab * 128 + 256; }
+
+// Clusters of npair Gram CTAs that are resident at once (cached per cluster size).
+int gram_max_clusters(int npair, int num_sms) {
+  static int cached[4] = {0, 0, 0, 0};
+  if (npair < 1 || npair > 3) return 1;
+  if (cached[npair] > 0) return cached[npair];
+  int n = 0;
+  const size_t smem = gram_smem();
+  if (cudaFuncSetAttribute(tc_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+      cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(npair * (num_sms / npair)));
+    cfg.blockDim = dim3(192);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)npair;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaOccupancyMaxActiveClusters(&n, tc_gram_kernel, &cfg) != cudaSuccess) n = 0;
+  }
+  cudaGetLastError();
+  if (n < 1) n = num_sms / npair;
+  if (n < 1) n = 1;
+  cached[npair] = n;
+  return n;
 }
 
 }  // namespace
@@ -815,8 +899,10 @@ int tc_gram(const __nv_bfloat16* Uh, const __nv_bfloat16* Ul, int64_t ldu, int k
             int64_t lda, int B, int dtype, int64_t M, int num_sms, double** partial,
             int64_t* partial_cap, int* status, cudaStream_t st) {
   if (dtype != PSVD_BF16) return PSVD_ERR_UNSUPPORTED;
-  GramGeom g = gram_geom(M, kc, B, num_sms);
-  if (g.np > 256 || M > 0x7fffffffll) return PSVD_ERR_SHAPE;
+  const int np = 2 * ((kc + 7) & ~7) + ((B + 7) & ~7);
+  if (np > 256 || M > 0x7fffffffll - 256) return PSVD_ERR_SHAPE;
+  const int npair = np > kSlab ? 3 : 1;
+  GramGeom g = gram_geom(M, kc, B, gram_max_clusters(npair, num_sms));
   PanelMaps pm;
   for (int wi = 0; wi < 4; ++wi) {
     const int bw = 64 >> wi;
@@ -848,17 +934,32 @@ int tc_gram(const __nv_bfloat16* Uh, const __nv_bfloat16* Ul, int64_t ldu, int k
   // columns of a block beyond the slab width are never written: keep them zero
   if (cudaMemsetAsync(*partial, 0, sizeof(double) * g.nrange * per, st) != cudaSuccess)
     return PSVD_ERR_CUDA;
-  const size_t smem = gram_smem(g);
+  const size_t smem = gram_smem();
   if (cudaFuncSetAttribute(tc_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
     return PSVD_ERR_CUDA;
-  const int grid = (int)(g.nrange * g.npair);
-  tc_gram_kernel<<<grid, 192, smem, st>>>(pm, g, *partial, status);
-  return cudaGetLastError() == cudaSuccess ? PSVD_OK : PSVD_ERR_CUDA;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(g.nrange * g.npair));
+  cfg.blockDim = dim3(192);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)g.npair;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, tc_gram_kernel, pm, g, *partial, status) != cudaSuccess) {
+    cudaGetLastError();
+    return PSVD_ERR_CUDA;
+  }
+  return PSVD_OK;
 }
 
 cudaError_t tc_gram_reduce(const double* partial, int64_t M, int kc, int B, int num_sms, double ff,
                            const double* D, double* G, double* H, int* status, cudaStream_t st) {
-  GramGeom g = gram_geom(M, kc, B, num_sms);
+  const int np = 2 * ((kc + 7) & ~7) + ((B + 7) & ~7);
+  GramGeom g = gram_geom(M, kc, B, gram_max_clusters(np > kSlab ? 3 : 1, num_sms));
   const int64_t per = (int64_t)g.npair * kSlab * kSlab;
   double* Ssum = const_cast<double*>(partial) + g.nrange * per;
   tc_gram_sum_kernel<<<(unsigned)ceil_div(per, 256), 256, 0, st>>>(partial, g.nrange, g.npair, Ssum);
