@@ -52,6 +52,11 @@ constexpr int kGramSubs = 2;
 // (K = 64, B = 128) stays within 5.3e-4 rad of the FP64 result (2.2e-3 with 16).
 // One slot (128 rows) is 8 MMAs.
 constexpr int kFoldStages = 1;
+// Gram CTA: warp 0 issues TMA loads, warp 1 issues MMAs, warps 2-3 only take part
+// in the CTA barriers, warps 4-11 drain TMEM (two per lane quadrant).  Twelve warps,
+// three per SM sub-partition, cap the registers at 168 per thread.
+constexpr int kGramEpiWarp0 = 4;
+constexpr int kGramThreads = (kGramEpiWarp0 + 8) * 32;
 constexpr int kUpdRows = 128;             // rows per update tile (UMMA M)
 constexpr int kUpdStages = 2;
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
@@ -170,18 +175,28 @@ __device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
       "h"(mask)
       : "memory");
 }
-// 32 consecutive TMEM columns of this thread's lane, without waiting.
-__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t* r) {
+// 16 consecutive TMEM columns of this thread's lane, without waiting.
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t* r) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
+}
+// Stores 16 consecutive TMEM columns of this thread's lane (no wait).
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+      "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+      "r"(__float_as_uint(v[15]))
+      : "memory");
 }
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
@@ -207,25 +222,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Stores 32 consecutive TMEM columns of this thread's lane (no wait).
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float* v) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
-      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
-      "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
-      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
-      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
-      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
-      "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
-      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
-      "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])),
-      "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])),
-      "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])),
-      "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])),
-      "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])),
-      "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
-      : "memory");
-}
 
 // Fast2Sum fold (Dekker): hi + lo accumulates x, lo collecting the rounding error of
 // hi + x.  The error term is exact when |hi| >= |x|, which holds for a running Gram
@@ -331,7 +327,7 @@ __device__ __forceinline__ void load_slab(const PanelMaps& pm, const GramGeom& g
 // and the epilogue, which folds each finished 128-row partial into a float-float
 // running sum (hi at column 256, lo at 384).  The block is written as FP64
 // (hi + lo) to partial[range][pair][128][128].
-__global__ void __launch_bounds__(192, 1) tc_gram_kernel(const __grid_constant__ PanelMaps pm,
+__global__ void __launch_bounds__(kGramThreads, 1) tc_gram_kernel(const __grid_constant__ PanelMaps pm,
                                                          GramGeom g, double* __restrict__ partial,
                                                          int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -367,7 +363,7 @@ __global__ void __launch_bounds__(192, 1) tc_gram_kernel(const __grid_constant__
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], 4);
+      mbar_init(&acc_empty[b], 8);
     }
     mbar_init(mma_done, 1);
     *abort_flag = 0;
@@ -480,11 +476,23 @@ __global__ void __launch_bounds__(192, 1) tc_gram_kernel(const __grid_constant__
       while (!mbar_try_wait(mma_done, 0) && clock64() - t0 < kWaitCycles) {
       }
     }
-  } else {
+  } else if (warp >= kGramEpiWarp0) {
     // ------------------------------------------------------------- epilogue
-    const int sub = warp & 3;
-    const uint32_t lane_base = tmem_base + ((uint32_t)(sub * 32) << 16);
-    const uint32_t t_hi = lane_base + 2 * kSlab, t_lo = lane_base + 3 * kSlab;
+    // Warps 4 .. 11: TMEM lane quadrant q = warp % 4 (block rows 32q .. 32q+31),
+    // column half ch (columns 64 ch .. 64 ch + 63).  The running hi sums live in
+    // registers, the lo sums in TMEM (columns 256 + 64 ch ..).  In a diagonal block
+    // a 32-column chunk wholly below the diagonal of the quadrant is skipped (the
+    // assembly reads the mirror entry).
+    const int q = warp & 3, ch = (warp - kGramEpiWarp0) >> 2;
+    const uint32_t lane_base = tmem_base + ((uint32_t)(q * 32) << 16);
+    const uint32_t t_lo = lane_base + 2 * kSlab + (uint32_t)(64 * ch);
+    bool need[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int c0 = 64 * ch + 32 * c;
+      need[c] = c0 < w && (!diag || c0 + 32 > 32 * q);
+    }
+    float hi[64];
     bool ok = true;
     for (int f = 0; f < nfold; ++f) {
       const int b = f & 1;
@@ -494,45 +502,46 @@ __global__ void __launch_bounds__(192, 1) tc_gram_kernel(const __grid_constant__
         break;
       }
       tc_fence_after();
-      for (int c0 = 0; c0 < w; c0 += 32) {
-        uint32_t a[32], h[32], l[32];
-        tmem_ld32_nowait(lane_base + (uint32_t)(b * kSlab + c0), a);
-        if (f > 0) {
-          tmem_ld32_nowait(t_hi + c0, h);
-          tmem_ld32_nowait(t_lo + c0, l);
-        }
-        tmem_wait_ld();
-        float fh[32], fl[32];
-        if (f == 0) {
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            fh[i] = __uint_as_float(a[i]);
-            fl[i] = 0.f;
-          }
-        } else {
+      for (int c = 0; c < 2; ++c) {
+        if (!need[c]) continue;
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            fh[i] = __uint_as_float(h[i]);
-            fl[i] = __uint_as_float(l[i]);
-            fold(fh[i], fl[i], __uint_as_float(a[i]));
+        for (int hf = 0; hf < 2; ++hf) {
+          const int cc = 32 * c + 16 * hf;  // column within this warp's 64
+          uint32_t a[16], l[16];
+          tmem_ld16_nowait(lane_base + (uint32_t)(b * kSlab + 64 * ch + cc), a);
+          if (f > 0) tmem_ld16_nowait(t_lo + cc, l);
+          tmem_wait_ld();
+          float fl[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            if (f == 0) {
+              hi[cc + i] = __uint_as_float(a[i]);
+              fl[i] = 0.f;
+            } else {
+              fl[i] = __uint_as_float(l[i]);
+              fold(hi[cc + i], fl[i], __uint_as_float(a[i]));
+            }
           }
+          tmem_st16(t_lo + cc, fl);
         }
-        tmem_st32(t_hi + c0, fh);
-        tmem_st32(t_lo + c0, fl);
       }
       tmem_wait_st();
       tc_fence_before();
+      __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[b]);
     }
     if (ok && nfold > 0) {
-      const int row_in_slab = sub * 32 + lane;
+      const int row_in_slab = q * 32 + lane;
       double* orow = partial + (((size_t)range * g.npair + pair) * kSlab + row_in_slab) * kSlab;
-      for (int c0 = 0; c0 < w; c0 += 32) {
-        float h[32], l[32];
-        tmem_ld32(t_hi + c0, h);
-        tmem_ld32(t_lo + c0, l);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) orow[c0 + i] = (double)h[i] + (double)l[i];
+      for (int c = 0; c < 2; ++c) {
+        if (!need[c]) continue;
+        float l[32];
+        tmem_ld32(t_lo + 32 * c, l);
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+          orow[64 * ch + 32 * c + i] = (double)hi[32 * c + i] + (double)l[i];
       }
     }
   }
@@ -572,8 +581,8 @@ __global__ void tc_gram_assemble_kernel(const double* __restrict__ Ssum, GramGeo
   double s = 0.0;
   for (int a = 0; a < ni; ++a)
     for (int b = 0; b < nj; ++b) {
-      int x = ci[a], y = cj[b];
-      if (x / kSlab > y / kSlab) { const int tmp = x; x = y; y = tmp; }
+      // each block holds its entries for x <= y (a diagonal block only those)
+      const int x = min(ci[a], cj[b]), y = max(ci[a], cj[b]);
       const int sx = x / kSlab, sy = y / kSlab;
       const int p = sx * g.nslab - sx * (sx - 1) / 2 + (sy - sx);
       s += Ssum[((size_t)p * kSlab + (x % kSlab)) * kSlab + (y % kSlab)];
@@ -865,7 +874,7 @@ int gram_max_clusters(int npair, int num_sms) {
       cudaSuccess) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(npair * (num_sms / npair)));
-    cfg.blockDim = dim3(192);
+    cfg.blockDim = dim3(kGramThreads);
     cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -939,7 +948,7 @@ int tc_gram(const __nv_bfloat16* Uh, const __nv_bfloat16* Ul, int64_t ldu, int k
     return PSVD_ERR_CUDA;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(g.nrange * g.npair));
-  cfg.blockDim = dim3(192);
+  cfg.blockDim = dim3(kGramThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
