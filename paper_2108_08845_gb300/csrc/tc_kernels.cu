@@ -502,29 +502,35 @@ __global__ void __launch_bounds__(kGramThreads, 1) tc_gram_kernel(const __grid_c
         break;
       }
       tc_fence_after();
+      // four 16-column pieces; the loads of piece p + 1 are in flight while piece p
+      // is folded (tcgen05.wait::ld waits for all of this thread's loads)
+      const int p_lo = need[0] ? 0 : 2, p_hi = need[1] ? 4 : 2;
+      uint32_t a[2][16], l[2][16];
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        if (!need[c]) continue;
-#pragma unroll
-        for (int hf = 0; hf < 2; ++hf) {
-          const int cc = 32 * c + 16 * hf;  // column within this warp's 64
-          uint32_t a[16], l[16];
-          tmem_ld16_nowait(lane_base + (uint32_t)(b * kSlab + 64 * ch + cc), a);
-          if (f > 0) tmem_ld16_nowait(t_lo + cc, l);
+      for (int p = 0; p < 4; ++p) {
+        if (p < p_lo || p >= p_hi) continue;
+        if (p == p_lo) {
+          tmem_ld16_nowait(lane_base + (uint32_t)(b * kSlab + 64 * ch + 16 * p), a[p & 1]);
+          if (f > 0) tmem_ld16_nowait(t_lo + 16 * p, l[p & 1]);
           tmem_wait_ld();
-          float fl[16];
-#pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            if (f == 0) {
-              hi[cc + i] = __uint_as_float(a[i]);
-              fl[i] = 0.f;
-            } else {
-              fl[i] = __uint_as_float(l[i]);
-              fold(hi[cc + i], fl[i], __uint_as_float(a[i]));
-            }
-          }
-          tmem_st16(t_lo + cc, fl);
         }
+        if (p + 1 < p_hi) {
+          tmem_ld16_nowait(lane_base + (uint32_t)(b * kSlab + 64 * ch + 16 * (p + 1)), a[(p + 1) & 1]);
+          if (f > 0) tmem_ld16_nowait(t_lo + 16 * (p + 1), l[(p + 1) & 1]);
+        }
+        float fl[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          if (f == 0) {
+            hi[16 * p + i] = __uint_as_float(a[p & 1][i]);
+            fl[i] = 0.f;
+          } else {
+            fl[i] = __uint_as_float(l[p & 1][i]);
+            fold(hi[16 * p + i], fl[i], __uint_as_float(a[p & 1][i]));
+          }
+        }
+        tmem_st16(t_lo + 16 * p, fl);
+        if (p + 1 < p_hi) tmem_wait_ld();
       }
       tmem_wait_st();
       tc_fence_before();
