@@ -32,8 +32,9 @@ struct psvd_ctx {
   int cur = 0;
   // FP32 modes (double-buffered) or BF16 hi/lo planes (tensor-core path)
   float* U[2] = {nullptr, nullptr};
-  __nv_bfloat16* Uh[2] = {nullptr, nullptr};
-  __nv_bfloat16* Ul[2] = {nullptr, nullptr};
+  // tensor-core path: both BF16 planes of the modes, slot-tiled (tc_kernels.cuh)
+  __nv_bfloat16* Ut[2] = {nullptr, nullptr};
+  int Kp = 0;  // column stride of the tiled planes, roundup(K, 8)
   double* D[2] = {nullptr, nullptr};
   double* partial = nullptr;
   int64_t partial_cap = 0;  // doubles
@@ -188,8 +189,8 @@ int panel_gram(psvd_ctx* h, const void* A, int64_t lda, int B, int dtype, int kc
                const double* D, double* G) {
   const int n = kc + B;
   if (use_tc(h)) {
-    int rc = tc_gram(h->Uh[h->cur], h->Ul[h->cur], h->ldu, kc, A, lda, B, dtype, h->M, h->num_sms,
-                     &h->partial, &h->partial_cap, &h->w.info[2], h->st);
+    int rc = tc_gram(h->Ut[h->cur], h->Kp, kc, A, lda, B, dtype, h->M, h->num_sms, &h->partial,
+                     &h->partial_cap, &h->w.info[2], h->st);
     if (rc) return rc;
     return tc_gram_reduce(h->partial, h->M, kc, B, h->num_sms, ff, D, G, h->w.H, &h->w.info[2],
                           h->st)
@@ -238,9 +239,8 @@ int step(psvd_ctx* h, const void* A, int64_t lda, int B, int dtype) {
   h->launches += nl;
   pr = prof_begin(h, 2);
   if (use_tc(h)) {
-    int rc = tc_update(h->Uh[h->cur], h->Ul[h->cur], h->ldu, kc, A, lda, B, dtype, h->M, T, n,
-                       k1, w.T3, h->Uh[h->cur ^ 1], h->Ul[h->cur ^ 1], h->num_sms, &h->w.info[2],
-                       h->st);
+    int rc = tc_update(h->Ut[h->cur], h->Kp, kc, A, lda, B, dtype, h->M, T, n, k1, w.T3,
+                       h->Ut[h->cur ^ 1], h->num_sms, &h->w.info[2], h->st);
     if (rc) return rc;
   } else {
     PanelF32 p{h->U[h->cur], h->ldu, kc, A, lda, dtype == PSVD_BF16 ? 1 : 0, h->M, n};
@@ -318,6 +318,7 @@ int psvd_create(psvd_handle* out, const psvd_config* cfg) {
   h->st = (cudaStream_t)cfg->stream;
   h->M = cfg->M;
   h->ldu = ceil_div(cfg->M, 64) * 64;
+  h->Kp = (cfg->K + 7) & ~7;
   h->K = cfg->K;
   h->maxB = cfg->max_batch;
   h->nmax = cfg->K + cfg->max_batch;
@@ -333,8 +334,7 @@ int psvd_create(psvd_handle* out, const psvd_config* cfg) {
   const size_t ucount = (size_t)h->ldu * (size_t)h->K;
   for (int b = 0; b < 2 && !rc; ++b) {
     if (use_tc(h)) {
-      rc = dalloc(&h->Uh[b], ucount);
-      if (!rc) rc = dalloc(&h->Ul[b], ucount);
+      rc = dalloc(&h->Ut[b], tc_modes_elems(h->M, h->K));
     } else {
       rc = dalloc(&h->U[b], ucount);
     }
@@ -375,9 +375,7 @@ int psvd_create(psvd_handle* out, const psvd_config* cfg) {
     // zero the mode buffers once so that padded rows stay zero
     for (int b = 0; b < 2 && !rc; ++b) {
       if (use_tc(h)) {
-        if (cudaMemsetAsync(h->Uh[b], 0, ucount * 2, h->st) ||
-            cudaMemsetAsync(h->Ul[b], 0, ucount * 2, h->st))
-          rc = PSVD_ERR_CUDA;
+        if (cudaMemsetAsync(h->Ut[b], 0, tc_modes_elems(h->M, h->K) * 2, h->st)) rc = PSVD_ERR_CUDA;
       } else if (cudaMemsetAsync(h->U[b], 0, ucount * 4, h->st)) {
         rc = PSVD_ERR_CUDA;
       }
@@ -402,8 +400,7 @@ void psvd_destroy(psvd_handle h) {
   }
   for (int b = 0; b < 2; ++b) {
     cudaFree(h->U[b]);
-    cudaFree(h->Uh[b]);
-    cudaFree(h->Ul[b]);
+    cudaFree(h->Ut[b]);
     cudaFree(h->D[b]);
   }
   cudaFree(h->partial);
@@ -469,7 +466,7 @@ int psvd_get_modes(psvd_handle h, float* U_out, int64_t ldo) {
   const float* src = h->U[h->cur];
   if (use_tc(h)) {
     if (!h->Uf32_tmp && dalloc(&h->Uf32_tmp, (size_t)h->ldu * h->K)) return PSVD_ERR_ALLOC;
-    CK(tc_modes_to_f32(h->Uh[h->cur], h->Ul[h->cur], h->ldu, h->M, h->kc, h->Uf32_tmp, h->st));
+    CK(tc_modes_to_f32(h->Ut[h->cur], h->Kp, h->M, h->kc, h->Uf32_tmp, h->ldu, h->st));
     src = h->Uf32_tmp;
   }
   CK(cudaMemcpy2DAsync(U_out, sizeof(float) * ldo, src, sizeof(float) * h->ldu,
@@ -600,12 +597,18 @@ int psvd_save(psvd_handle h, const char* path) {
   // TC handles keep the exact hi/lo pair: save it too so a reload is bit-identical
   unsigned short* hl = nullptr;
   if (rc >= 0 && use_tc(h)) {
+    // file layout: Uh then Ul, each M x kc column-major
+    const size_t nt = tc_modes_elems(h->M, h->K);
     hl = (unsigned short*)malloc(sizeof(unsigned short) * 2 * (nu ? nu : 1));
-    if (!hl) rc = PSVD_ERR_ALLOC;
-    if (rc >= 0 &&
-        (cudaMemcpy2D(hl, 2 * h->M, h->Uh[h->cur], 2 * h->ldu, 2 * h->M, h->kc, cudaMemcpyDeviceToHost) ||
-         cudaMemcpy2D(hl + nu, 2 * h->M, h->Ul[h->cur], 2 * h->ldu, 2 * h->M, h->kc, cudaMemcpyDeviceToHost)))
-      rc = PSVD_ERR_CUDA;
+    unsigned short* tiled = (unsigned short*)malloc(sizeof(unsigned short) * nt);
+    if (!hl || !tiled) rc = PSVD_ERR_ALLOC;
+    if (rc >= 0 && cudaMemcpy(tiled, h->Ut[h->cur], 2 * nt, cudaMemcpyDeviceToHost)) rc = PSVD_ERR_CUDA;
+    if (rc >= 0)
+      for (int p = 0; p < 2; ++p)
+        for (int c = 0; c < h->kc; ++c)
+          for (int64_t r = 0; r < h->M; ++r)
+            hl[p * nu + (size_t)c * h->M + r] = tiled[tc_mode_index(r, p, c, h->Kp)];
+    free(tiled);
   }
   FILE* f = nullptr;
   if (rc >= 0) f = fopen(path, "wb");
@@ -647,6 +650,8 @@ int psvd_load(psvd_handle* out, const char* path, void* stream) {
   if (!rc) {
     c.stream = stream;
     rc = psvd_create(&h, &c);
+    // the buffers are zeroed on the handle's stream: finish that before the copies
+    if (!rc && cudaStreamSynchronize(h->st) != cudaSuccess) rc = PSVD_ERR_CUDA;
   }
   const size_t nu = rc ? 0 : (size_t)c.M * kc;
   float* U = rc ? nullptr : (float*)malloc(sizeof(float) * nu);
@@ -662,9 +667,19 @@ int psvd_load(psvd_handle* out, const char* path, void* stream) {
   fclose(f);
   if (!rc) {
     if (use_tc(h)) {
-      if (cudaMemcpy2D(h->Uh[0], 2 * h->ldu, hl, 2 * c.M, 2 * c.M, kc, cudaMemcpyHostToDevice) ||
-          cudaMemcpy2D(h->Ul[0], 2 * h->ldu, hl + nu, 2 * c.M, 2 * c.M, kc, cudaMemcpyHostToDevice))
-        rc = PSVD_ERR_CUDA;
+      // rows beyond M and columns beyond kc stay zero
+      const size_t nt = tc_modes_elems(c.M, c.K);
+      unsigned short* tiled = (unsigned short*)calloc(nt, sizeof(unsigned short));
+      if (!tiled) {
+        rc = PSVD_ERR_ALLOC;
+      } else {
+        for (int p = 0; p < 2; ++p)
+          for (int cc = 0; cc < kc; ++cc)
+            for (int64_t r = 0; r < c.M; ++r)
+              tiled[tc_mode_index(r, p, cc, h->Kp)] = hl[p * nu + (size_t)cc * c.M + r];
+        if (cudaMemcpy(h->Ut[0], tiled, 2 * nt, cudaMemcpyHostToDevice)) rc = PSVD_ERR_CUDA;
+        free(tiled);
+      }
     } else if (cudaMemcpy2D(h->U[0], 4 * h->ldu, U, 4 * c.M, 4 * c.M, kc, cudaMemcpyHostToDevice)) {
       rc = PSVD_ERR_CUDA;
     }

@@ -2,7 +2,8 @@
 // Algorithm 1 (Sec. 3.1).
 //
 // The modes are stored as a pair of BF16 planes, U = Uh + Ul (16 significant
-// bits), the snapshots A in BF16, so the padded panel
+// bits), slot-tiled (tc_kernels.cuh), the snapshots A in BF16 column-major, so the
+// padded panel
 //     P' = [Uh (kcp cols) | Ul (kcp cols) | A (Bp cols)],  kcp = roundup(kc, 8)
 // is an exact BF16 representation of [U | A] and every product on the tensor
 // cores is exact; accumulation is FP32 in tensor memory (TMEM).
@@ -265,6 +266,7 @@ struct GramGeom {
   int np;      // 2*kcp + Bp
   int nslab;   // ceil(np / 128)
   int npair;   // nslab*(nslab+1)/2
+  int Kp;              // column stride of the tiled mode planes
   int64_t nslot;       // 128-row slots covering M
   int64_t nrange;      // clusters; cluster r takes slots r, r + nrange, ...
   int fold_stages;     // 64-row stages (4 MMAs each) per FP32 accumulation chain
@@ -293,7 +295,10 @@ __device__ __forceinline__ int slab_width16(int s, int np) {
 
 // Loads slab s (padded-panel columns [128 s, 128 s + 128)) for rows [row, row + 64)
 // into dst: each plane's column range inside the slab is tiled by boxes of 64,
-// 32, 16 and 8 columns.  mask != 0: multicast to those CTAs of the cluster.
+// 32, 16 and 8 columns.  The mode planes (src 0, 1) are slot-tiled: their box
+// starts at line ((row / 128 * 2 + row / 64 % 2) * 2 + src) * Kp + column; the
+// snapshots (src 2) are column-major.  mask != 0: multicast to those CTAs of the
+// cluster.
 __device__ __forceinline__ void load_slab(const PanelMaps& pm, const GramGeom& g, int s,
                                           uint64_t* bar, uint8_t* dst, int row, uint16_t mask) {
   const int lo = s * kSlab, hi = min(g.np, (s + 1) * kSlab);
@@ -305,10 +310,15 @@ __device__ __forceinline__ void load_slab(const PanelMaps& pm, const GramGeom& g
     while (c < c_end) {
       const int left = c_end - c;
       const int wi = left >= 64 ? 0 : left >= 32 ? 1 : left >= 16 ? 2 : 3;
+      int x = row, y = c - start[src];
+      if (src < 2) {
+        x = 0;
+        y += (((row >> 7) * 2 + ((row >> 6) & 1)) * 2 + src) * g.Kp;
+      }
       if (mask)
-        tma_load_2d_mc(&pm.m[src][wi], bar, dst + (c - lo) * 128, row, c - start[src], mask);
+        tma_load_2d_mc(&pm.m[src][wi], bar, dst + (c - lo) * 128, x, y, mask);
       else
-        tma_load_2d(&pm.m[src][wi], bar, dst + (c - lo) * 128, row, c - start[src]);
+        tma_load_2d(&pm.m[src][wi], bar, dst + (c - lo) * 128, x, y);
       c += 64 >> wi;
     }
   }
@@ -611,7 +621,7 @@ struct UpdGeom {
   int N;            // 3 * k1p
   int nkb;          // K blocks of 64 panel columns: ceil(np / 64)
   int64_t ntiles;   // row tiles of 128
-  int64_t ldu;
+  int Kp;           // column stride of the tiled mode planes
 };
 
 // T3 (N x npk row-major BF16, npk = 64 * nkb): row part*k1p + j, column = padded
@@ -638,12 +648,10 @@ __global__ void tc_pack_T_kernel(const float* __restrict__ T, int n, int kc, Upd
   T3[e] = __float2bfloat16_rn(v);
 }
 
-__global__ void __launch_bounds__(192, 1) tc_update_kernel(const __grid_constant__ CUtensorMap mUh,
-                                                           const __grid_constant__ CUtensorMap mUl,
+__global__ void __launch_bounds__(192, 1) tc_update_kernel(const __grid_constant__ CUtensorMap mU,
                                                            const __grid_constant__ CUtensorMap mA,
                                                            const __grid_constant__ CUtensorMap mT,
-                                                           UpdGeom u, __nv_bfloat16* __restrict__ Uh_new,
-                                                           __nv_bfloat16* __restrict__ Ul_new,
+                                                           UpdGeom u, __nv_bfloat16* __restrict__ Ut_new,
                                                            int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -701,8 +709,9 @@ __global__ void __launch_bounds__(192, 1) tc_update_kernel(const __grid_constant
           const int row = (int)(t * kUpdRows + h * 64);
           uint8_t* d = dst + h * half_bytes;
           if (u.kcp > 0) {
-            tma_load_2d(&mUh, &full[stage], d, row, 0);
-            tma_load_2d(&mUl, &full[stage], d + u.kcp * 128, row, 0);
+            const int y = (int)((t * 2 + h) * 2) * u.Kp;
+            tma_load_2d(&mU, &full[stage], d, 0, y);
+            tma_load_2d(&mU, &full[stage], d + u.kcp * 128, 0, y + u.Kp);
           }
           tma_load_2d(&mA, &full[stage], d + 2 * u.kcp * 128, row, 0);
         }
@@ -787,8 +796,8 @@ __global__ void __launch_bounds__(192, 1) tc_update_kernel(const __grid_constant
               const float v = (h[i] + m[i]) + l[i];
               const __nv_bfloat16 vh = __float2bfloat16_rn(v);
               const __nv_bfloat16 vl = __float2bfloat16_rn(v - __bfloat162float(vh));
-              Uh_new[row + (int64_t)j * u.ldu] = vh;
-              Ul_new[row + (int64_t)j * u.ldu] = vl;
+              Ut_new[tc_mode_index(row, 0, j, u.Kp)] = vh;
+              Ut_new[tc_mode_index(row, 1, j, u.Kp)] = vl;
             }
           }
         }
@@ -803,13 +812,13 @@ __global__ void __launch_bounds__(192, 1) tc_update_kernel(const __grid_constant
   if (warp == 1) tmem_dealloc(tmem_base, 512);
 }
 
-__global__ void tc_modes_to_f32_kernel(const __nv_bfloat16* __restrict__ Uh,
-                                       const __nv_bfloat16* __restrict__ Ul, int64_t ldu, int64_t M,
-                                       int k, float* __restrict__ out) {
+__global__ void tc_modes_to_f32_kernel(const __nv_bfloat16* __restrict__ Ut, int Kp, int64_t M,
+                                       int k, float* __restrict__ out, int64_t ldo) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= M * k) return;
   const int64_t r = e % M, c = e / M;
-  out[r + c * ldu] = __bfloat162float(Uh[r + c * ldu]) + __bfloat162float(Ul[r + c * ldu]);
+  out[r + c * ldo] = __bfloat162float(Ut[tc_mode_index(r, 0, (int)c, Kp)]) +
+                     __bfloat162float(Ut[tc_mode_index(r, 1, (int)c, Kp)]);
 }
 
 // ---------------------------------------------------------------- host side
@@ -849,9 +858,24 @@ bool make_map(CUtensorMap* m, const void* ptr, int64_t rows, int64_t cols, int64
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-GramGeom gram_geom(int64_t M, int kc, int B, int max_clusters) {
+// 2-D BF16 tensor map of a tiled mode buffer seen as nlines lines of 64 elements
+// (128 bytes), box = box_lines lines, 128-byte swizzle.
+bool make_map_lines(CUtensorMap* m, const void* ptr, int64_t nlines, int box_lines) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || box_lines < 1 || box_lines > 256 || ((uintptr_t)ptr & 15)) return false;
+  const cuuint64_t dims[2] = {64, (cuuint64_t)nlines};
+  const cuuint64_t strides[1] = {128};
+  const cuuint32_t box[2] = {64u, (cuuint32_t)box_lines};
+  const cuuint32_t estr[2] = {1u, 1u};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+GramGeom gram_geom(int64_t M, int kc, int B, int max_clusters, int Kp) {
   GramGeom g;
   g.M = M;
+  g.Kp = Kp;
   g.kcp = (kc + 7) & ~7;
   g.Bp = (B + 7) & ~7;
   g.np = 2 * g.kcp + g.Bp;
@@ -910,21 +934,27 @@ namespace {
 
 }  // namespace
 
-int tc_gram(const __nv_bfloat16* Uh, const __nv_bfloat16* Ul, int64_t ldu, int kc, const void* A,
-            int64_t lda, int B, int dtype, int64_t M, int num_sms, double** partial,
-            int64_t* partial_cap, int* status, cudaStream_t st) {
+size_t tc_modes_elems(int64_t M, int K) {
+  return (size_t)ceil_div(M, (int64_t)128) * 4 * (size_t)((K + 7) & ~7) * 64;
+}
+
+int tc_gram(const __nv_bfloat16* Ut, int Kp, int kc, const void* A, int64_t lda, int B, int dtype,
+            int64_t M, int num_sms, double** partial, int64_t* partial_cap, int* status,
+            cudaStream_t st) {
   if (dtype != PSVD_BF16) return PSVD_ERR_UNSUPPORTED;
   const int np = 2 * ((kc + 7) & ~7) + ((B + 7) & ~7);
   if (np > 256 || M > 0x7fffffffll - 256) return PSVD_ERR_SHAPE;
   const int npair = np > kSlab ? 3 : 1;
-  GramGeom g = gram_geom(M, kc, B, gram_max_clusters(npair, num_sms));
+  if (kc > Kp) return PSVD_ERR_SHAPE;
+  GramGeom g = gram_geom(M, kc, B, gram_max_clusters(npair, num_sms), Kp);
   PanelMaps pm;
+  const int64_t nlines = ceil_div(M, (int64_t)128) * 4 * Kp;
   for (int wi = 0; wi < 4; ++wi) {
     const int bw = 64 >> wi;
     if (!make_map(&pm.m[2][wi], A, M, B, lda, bw)) return PSVD_ERR_INVALID_ARG;
     if (kc > 0) {
-      if (!make_map(&pm.m[0][wi], Uh, M, kc, ldu, bw) || !make_map(&pm.m[1][wi], Ul, M, kc, ldu, bw))
-        return PSVD_ERR_INVALID_ARG;
+      if (!make_map_lines(&pm.m[0][wi], Ut, nlines, bw)) return PSVD_ERR_INVALID_ARG;
+      pm.m[1][wi] = pm.m[0][wi];
     } else {
       pm.m[0][wi] = pm.m[2][wi];
       pm.m[1][wi] = pm.m[2][wi];
@@ -974,7 +1004,7 @@ int tc_gram(const __nv_bfloat16* Uh, const __nv_bfloat16* Ul, int64_t ldu, int k
 cudaError_t tc_gram_reduce(const double* partial, int64_t M, int kc, int B, int num_sms, double ff,
                            const double* D, double* G, double* H, int* status, cudaStream_t st) {
   const int np = 2 * ((kc + 7) & ~7) + ((B + 7) & ~7);
-  GramGeom g = gram_geom(M, kc, B, gram_max_clusters(np > kSlab ? 3 : 1, num_sms));
+  GramGeom g = gram_geom(M, kc, B, gram_max_clusters(np > kSlab ? 3 : 1, num_sms), 0);
   const int64_t per = (int64_t)g.npair * kSlab * kSlab;
   double* Ssum = const_cast<double*>(partial) + g.nrange * per;
   tc_gram_sum_kernel<<<(unsigned)ceil_div(per, 256), 256, 0, st>>>(partial, g.nrange, g.npair, Ssum);
@@ -987,10 +1017,9 @@ cudaError_t tc_gram_reduce(const double* partial, int64_t M, int kc, int B, int 
   return cudaGetLastError();
 }
 
-int tc_update(const __nv_bfloat16* Uh, const __nv_bfloat16* Ul, int64_t ldu, int kc, const void* A,
-              int64_t lda, int B, int dtype, int64_t M, const float* T, int n, int k1,
-              __nv_bfloat16* T3, __nv_bfloat16* Uh_new, __nv_bfloat16* Ul_new, int num_sms,
-              int* status, cudaStream_t st) {
+int tc_update(const __nv_bfloat16* Ut, int Kp, int kc, const void* A, int64_t lda, int B, int dtype,
+              int64_t M, const float* T, int n, int k1, __nv_bfloat16* T3, __nv_bfloat16* Ut_new,
+              int num_sms, int* status, cudaStream_t st) {
   if (dtype != PSVD_BF16) return PSVD_ERR_UNSUPPORTED;
   UpdGeom u;
   u.M = M;
@@ -1003,21 +1032,20 @@ int tc_update(const __nv_bfloat16* Uh, const __nv_bfloat16* Ul, int64_t ldu, int
   u.N = 3 * u.k1p;
   u.nkb = (int)ceil_div(u.np, 64);
   u.ntiles = ceil_div(M, kUpdRows);
-  u.ldu = ldu;
+  u.Kp = Kp;
   if (u.np > 256 || u.N > 256 || M > 0x7fffffffll) return PSVD_ERR_SHAPE;
   const int npk = u.nkb * 64;
   const int64_t tcount = (int64_t)u.N * npk;
   tc_pack_T_kernel<<<(unsigned)ceil_div(tcount, 256), 256, 0, st>>>(T, n, kc, u, npk, T3);
   if (cudaGetLastError() != cudaSuccess) return PSVD_ERR_CUDA;
-  CUtensorMap mUh, mUl, mA, mT;
+  CUtensorMap mU, mA, mT;
   // the A operand spans np (16-padded) columns: the maps deliver zeros past the data
   if (!make_map(&mA, A, M, B, lda, u.np - 2 * u.kcp)) return PSVD_ERR_INVALID_ARG;
   if (kc > 0) {
-    if (!make_map(&mUh, Uh, M, kc, ldu, u.kcp) || !make_map(&mUl, Ul, M, kc, ldu, u.kcp))
+    if (u.kcp > Kp || !make_map_lines(&mU, Ut, ceil_div(M, (int64_t)128) * 4 * Kp, u.kcp))
       return PSVD_ERR_INVALID_ARG;
   } else {
-    mUh = mA;
-    mUl = mA;
+    mU = mA;
   }
   // T3 is N rows x npk columns, row-major: a "column-major" npk x N matrix
   if (!make_map(&mT, T3, npk, u.N, npk, u.N)) return PSVD_ERR_INVALID_ARG;
@@ -1026,15 +1054,15 @@ int tc_update(const __nv_bfloat16* Uh, const __nv_bfloat16* Ul, int64_t ldu, int
   if (cudaFuncSetAttribute(tc_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
     return PSVD_ERR_CUDA;
   const int grid = (int)(u.ntiles < num_sms ? u.ntiles : num_sms);
-  tc_update_kernel<<<grid, 192, smem, st>>>(mUh, mUl, mA, mT, u, Uh_new, Ul_new, status);
+  tc_update_kernel<<<grid, 192, smem, st>>>(mU, mA, mT, u, Ut_new, status);
   return cudaGetLastError() == cudaSuccess ? PSVD_OK : PSVD_ERR_CUDA;
 }
 
-cudaError_t tc_modes_to_f32(const __nv_bfloat16* Uh, const __nv_bfloat16* Ul, int64_t ldu,
-                            int64_t M, int k, float* out, cudaStream_t st) {
+cudaError_t tc_modes_to_f32(const __nv_bfloat16* Ut, int Kp, int64_t M, int k, float* out,
+                            int64_t ldo, cudaStream_t st) {
   const int64_t tot = M * k;
   if (tot == 0) return cudaSuccess;
-  tc_modes_to_f32_kernel<<<(unsigned)ceil_div(tot, 256), 256, 0, st>>>(Uh, Ul, ldu, M, k, out);
+  tc_modes_to_f32_kernel<<<(unsigned)ceil_div(tot, 256), 256, 0, st>>>(Ut, Kp, M, k, out, ldo);
   return cudaGetLastError();
 }
 

@@ -5,25 +5,36 @@
 
 namespace psvd {
 
-// Partial Grams of the panel [Uh | Ul | A] (BF16; U = Uh + Ul) over row chunks,
-// written to *partial (grown if needed).  A timed-out wait ORs 8 into *status.
-// Returns a PSVD status.
-int tc_gram(const __nv_bfloat16* Uh, const __nv_bfloat16* Ul, int64_t ldu, int kc, const void* A,
-            int64_t lda, int B, int dtype, int64_t M, int num_sms, double** partial,
-            int64_t* partial_cap, int* status, cudaStream_t st);
+// Modes of the tensor-core path: U = Uh + Ul (two BF16 planes) stored slot-tiled.
+// For every block of 128 rows, 64-row half h and plane p (0: Uh, 1: Ul), column c
+// (c < Kp = roundup(K, 8)) holds its 64 rows as one contiguous 128-byte line, so
+// a run of columns of one half and plane is contiguous memory and TMA streams it
+// at the HBM rate (a column-major panel, with its columns M rows apart, is
+// capped well below it by address translation).  Rows beyond M are zero.
+__host__ __device__ inline int64_t tc_mode_index(int64_t row, int plane, int col, int Kp) {
+  return ((((row >> 7) * 2 + ((row >> 6) & 1)) * 2 + plane) * (int64_t)Kp + col) * 64 + (row & 63);
+}
+// BF16 elements of one tiled mode buffer (both planes) for M rows and K modes.
+size_t tc_modes_elems(int64_t M, int K);
+// Partial Grams of the panel [Uh | Ul | A] (BF16; U = Uh + Ul, tiled as above with
+// column stride Kp) over row slots, written to *partial (grown if needed).  A
+// timed-out wait ORs 8 into *status.  Returns a PSVD status.
+int tc_gram(const __nv_bfloat16* Ut, int Kp, int kc, const void* A, int64_t lda, int B, int dtype,
+            int64_t M, int num_sms, double** partial, int64_t* partial_cap, int* status,
+            cudaStream_t st);
 // G = fixed-order FP64 sum of the partials (U^T U from the hi/lo blocks), H = S G S.
 cudaError_t tc_gram_reduce(const double* partial, int64_t M, int kc, int B, int num_sms, double ff,
                            const double* D, double* G, double* H, int* status, cudaStream_t st);
 // BF16 elements of the packed update coefficients for K modes and batches <= maxB.
 size_t tc_t3_elems(int K, int maxB);
-// [Uh_new + Ul_new] = [Uh | Ul | A] * T on the tensor cores: T (n x k1 FP32, ld n) is
-// split exactly into three BF16 parts packed into T3 (tc_t3_elems) first.
-int tc_update(const __nv_bfloat16* Uh, const __nv_bfloat16* Ul, int64_t ldu, int kc, const void* A,
-              int64_t lda, int B, int dtype, int64_t M, const float* T, int n, int k1,
-              __nv_bfloat16* T3, __nv_bfloat16* Uh_new, __nv_bfloat16* Ul_new, int num_sms,
-              int* status, cudaStream_t st);
-// out = float(Uh) + float(Ul) (exact), M x k, ld ldu.
-cudaError_t tc_modes_to_f32(const __nv_bfloat16* Uh, const __nv_bfloat16* Ul, int64_t ldu,
-                            int64_t M, int k, float* out, cudaStream_t st);
+// Ut_new = [Uh | Ul | A] * T on the tensor cores (modes tiled, column stride Kp):
+// T (n x k1 FP32, ld n) is split exactly into three BF16 parts packed into T3
+// (tc_t3_elems) first.
+int tc_update(const __nv_bfloat16* Ut, int Kp, int kc, const void* A, int64_t lda, int B, int dtype,
+              int64_t M, const float* T, int n, int k1, __nv_bfloat16* T3, __nv_bfloat16* Ut_new,
+              int num_sms, int* status, cudaStream_t st);
+// out = float(Uh) + float(Ul) (exact), M x k column-major with leading dimension ldo.
+cudaError_t tc_modes_to_f32(const __nv_bfloat16* Ut, int Kp, int64_t M, int k, float* out,
+                            int64_t ldo, cudaStream_t st);
 
 }  // namespace psvd
