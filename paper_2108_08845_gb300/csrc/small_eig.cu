@@ -156,6 +156,8 @@ __global__ void __launch_bounds__(LT) level_eig_kernel(LevelArgs a) {
         const int i = r0 + r, j = c0 + c;
         at[r][c] = (i < m && j < m) ? A[i + j * LDA] : 0.f;
       }
+    // the reflector buffer starts at zero; (b) then rewrites entries k .. m-1
+    for (int i = tid; i < kMaxN; i += LT) uvec[i] = 0.f;
     for (int k = 0; k < m - 2; ++k) {
       // (a) column k below the diagonal, and d[k]
       if (lane == k / TRC) {
@@ -173,12 +175,22 @@ __global__ void __launch_bounds__(LT) level_eig_kernel(LevelArgs a) {
           }
       }
       __syncthreads();
-      // (b) reflector from xcol[k+1 .. m-1]
+      // (b) reflector from xcol[k+1 .. m-1]: one warp, element i = k+1+lane+32j
+      //     in xv[j]; loads issued together and the sum taken as a tree (this
+      //     step is a serial chain that the other warps wait for)
       if (warp == 0) {
-        float sq = 0.f;
-        for (int i = k + 2 + lane; i < m; i += 32) sq = fmaf(xcol[i], xcol[i], sq);
-        sq = warp_sum(sq);
-        const float x0 = xcol[k + 1];
+        float xv[TRC];
+#pragma unroll
+        for (int j = 0; j < TRC; ++j) {
+          const int i = k + 1 + lane + 32 * j;
+          xv[j] = i < m ? xcol[i] : 0.f;
+        }
+        const float x0 = __shfl_sync(0xffffffffu, xv[0], 0);  // xcol[k+1]
+        float s01 = lane == 0 ? 0.f : xv[0] * xv[0];
+        s01 = fmaf(xv[1], xv[1], s01);
+        const float s23 = fmaf(xv[3], xv[3], xv[2] * xv[2]);
+        const float s45 = fmaf(xv[5], xv[5], xv[4] * xv[4]);
+        const float sq = warp_sum((s01 + s23) + s45);
         const bool refl = sq > 0.f && isfinite(sq);
         float alpha = x0, inv = 0.f, v0 = 0.f;
         if (refl) {
@@ -187,10 +199,17 @@ __global__ void __launch_bounds__(LT) level_eig_kernel(LevelArgs a) {
           v0 = x0 - alpha;
           inv = rsqrtf(fmaf(v0, v0, sq));
         }
-        for (int i = lane; i < kMaxN; i += 32) {
-          const float ui = (!refl || i <= k || i >= m) ? 0.f : (i == k + 1) ? v0 * inv : xcol[i] * inv;
-          uvec[i] = ui;
-          if (i > k && i < m) a.V[i + (int64_t)k * ldz] = ui;
+        // entries <= k were zeroed when their columns were reduced; uvec[k] is
+        // the previous reflector's first entry
+        if (lane == 0) uvec[k] = 0.f;
+#pragma unroll
+        for (int j = 0; j < TRC; ++j) {
+          const int i = k + 1 + lane + 32 * j;
+          if (i < m) {
+            const float ui = !refl ? 0.f : (i == k + 1) ? v0 * inv : xv[j] * inv;
+            uvec[i] = ui;
+            a.V[i + (int64_t)k * ldz] = ui;
+          }
         }
         if (lane == 0) {
           e[k] = alpha;
