@@ -80,7 +80,7 @@ struct LevelArgs {
 
 __global__ void __launch_bounds__(LT) level_eig_kernel(LevelArgs a) {
   extern __shared__ __align__(16) float smem[];
-  __shared__ float d[kMaxN], e[kMaxN], e2[kMaxN], lamf[kMaxN], beta[kMaxN], qbeta[kMaxN];
+  __shared__ float d[kMaxN], e[kMaxN], e2[kMaxN], lamf[kMaxN], qbeta[kMaxN];
   __shared__ float red[LW];
   __shared__ int cl_start[kMaxN + 1], cl_of[kMaxN], fb[kMaxN];
   __shared__ int s_ncl, s_r, s_b, s_go;
@@ -111,10 +111,21 @@ __global__ void __launch_bounds__(LT) level_eig_kernel(LevelArgs a) {
 
   // ---- 0. load the block, scaled by a power of two so that FP32 neither
   //         overflows nor underflows
+  // warp w takes columns w, w + 16, ...; lane l rows l, l + 32, ... (all loads of a
+  // column issued before they are used)
+  constexpr int NQ = kMaxN / 32;
   float amax_l = 0.f;
-  for (int j = warp; j < m; j += LW)
-    for (int i = lane; i < m; i += 32)
-      amax_l = fmaxf(amax_l, (float)fabs(Hf[(b + i) + (int64_t)(b + j) * n]));
+  for (int j = warp; j < m; j += LW) {
+    const double* col = Hf + b + (int64_t)(b + j) * n;
+    double v[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const int i = lane + 32 * q;
+      v[q] = i < m ? col[i] : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) amax_l = fmaxf(amax_l, (float)fabs(v[q]));
+  }
   amax_l = warp_max(amax_l);
   if (lane == 0) red[warp] = amax_l;
   __syncthreads();
@@ -127,8 +138,20 @@ __global__ void __launch_bounds__(LT) level_eig_kernel(LevelArgs a) {
   }
   __syncthreads();
   const double sc = s_scale;
-  for (int j = warp; j < m; j += LW)
-    for (int i = lane; i < m; i += 32) A[i + j * LDA] = (float)(Hf[(b + i) + (int64_t)(b + j) * n] * sc);
+  for (int j = warp; j < m; j += LW) {
+    const double* col = Hf + b + (int64_t)(b + j) * n;
+    double v[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const int i = lane + 32 * q;
+      v[q] = i < m ? col[i] : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const int i = lane + 32 * q;
+      if (i < m) A[i + j * LDA] = (float)(v[q] * sc);
+    }
+  }
   __syncthreads();
 
   // ---- 1. Householder tridiagonalisation with the matrix in registers: thread
@@ -213,7 +236,6 @@ __global__ void __launch_bounds__(LT) level_eig_kernel(LevelArgs a) {
         }
         if (lane == 0) {
           e[k] = alpha;
-          beta[k] = refl ? 2.f : 0.f;
           a.vb[k] = refl ? 2.f : 0.f;
           s_reflect = refl ? 1 : 0;
         }
@@ -288,8 +310,6 @@ __global__ void __launch_bounds__(LT) level_eig_kernel(LevelArgs a) {
   }
   __syncthreads();
   if (tid == 0) {
-    if (m >= 2) beta[m - 2] = 0.f;
-    beta[m - 1] = 0.f;
     e[m - 1] = 0.f;
     for (int k = max(m - 2, 0); k < m; ++k) a.vb[k] = 0.f;
     float gl = INFINITY, gu = -INFINITY, emax2 = 0.f;
@@ -623,10 +643,20 @@ __global__ void __launch_bounds__(LT) level_eig_kernel(LevelArgs a) {
     // t + 1 from its now updated column, so one block barrier per step suffices
     auto form_reflector = [&](int t) {
       float* zc = Zq + t * m;
-      float s = 0.f;
-      for (int i = t + 1 + lane; i < m; i += 32) s = fmaf(zc[i], zc[i], s);
-      const float s1 = warp_sum(s);
+      float zv[NE];
+#pragma unroll
+      for (int q = 0; q < NE; ++q) {
+        const int i = lane + 32 * q;
+        zv[q] = (i >= t && i < m) ? zc[i] : 0.f;
+      }
       const float x0 = zc[t];
+      float s = 0.f;
+#pragma unroll
+      for (int q = 0; q < NE; ++q) {
+        const int i = lane + 32 * q;
+        s = fmaf(i > t ? zv[q] : 0.f, zv[q], s);
+      }
+      const float s1 = warp_sum(s);
       float bt = 0.f, v0 = x0, inv = 1.f;
       if (s1 > 0.f && isfinite(s1)) {  // unit reflector u = v / ||v||, H = I - 2 u u^T
         const float nrm = sqrtf(fmaf(x0, x0, s1));
@@ -635,8 +665,13 @@ __global__ void __launch_bounds__(LT) level_eig_kernel(LevelArgs a) {
         bt = 2.f;
       }
       __syncwarp();
-      if (bt != 0.f)
-        for (int i = t + lane; i < m; i += 32) zc[i] = (i == t) ? v0 * inv : zc[i] * inv;
+      if (bt != 0.f) {
+#pragma unroll
+        for (int q = 0; q < NE; ++q) {
+          const int i = lane + 32 * q;
+          if (i >= t && i < m) zc[i] = (i == t) ? v0 * inv : zv[q] * inv;
+        }
+      }
       if (lane == 0) qbeta[t] = bt;
       __syncwarp();
     };
@@ -646,45 +681,101 @@ __global__ void __launch_bounds__(LT) level_eig_kernel(LevelArgs a) {
       const float bt = qbeta[t];
       const float* zc = Zq + t * m;
       int c0 = t + 1 + ((warp - (t + 1)) % LW + LW) % LW;  // first c > t owned by this warp
-      for (int c = c0; c < r; c += LW) {
-        if (bt != 0.f) {
-          float* zk = Zq + c * m;
-          float dt = 0.f;
-          for (int i = t + lane; i < m; i += 32) dt = fmaf(zc[i], zk[i], dt);
-          dt = warp_sum(dt) * bt;
-          for (int i = t + lane; i < m; i += 32) zk[i] = fmaf(-dt, zc[i], zk[i]);
-          __syncwarp();
+      if (bt != 0.f && c0 < r) {
+        float zv[NE];
+#pragma unroll
+        for (int q = 0; q < NE; ++q) {
+          const int i = lane + 32 * q;
+          zv[q] = (i >= t && i < m) ? zc[i] : 0.f;
         }
+        // this warp's columns c0, c0 + 16, ..., four at a time: dot products and
+        // warp sums interleaved
+        for (int cb = c0; cb < r; cb += 4 * LW) {
+          float dt[4];
+#pragma unroll
+          for (int w4 = 0; w4 < 4; ++w4) {
+            const int c = cb + w4 * LW;
+            float acc = 0.f;
+            if (c < r) {
+              const float* zk = Zq + c * m;
+#pragma unroll
+              for (int q = 0; q < NE; ++q) {
+                const int i = lane + 32 * q;
+                acc = fmaf(zv[q], (i < m) ? zk[i] : 0.f, acc);
+              }
+            }
+            dt[w4] = acc;
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int w4 = 0; w4 < 4; ++w4) dt[w4] += __shfl_xor_sync(0xffffffffu, dt[w4], o);
+#pragma unroll
+          for (int w4 = 0; w4 < 4; ++w4) {
+            const int c = cb + w4 * LW;
+            if (c < r) {
+              float* zk = Zq + c * m;
+              const float f = dt[w4] * bt;
+#pragma unroll
+              for (int q = 0; q < NE; ++q) {
+                const int i = lane + 32 * q;
+                if (i >= t && i < m) zk[i] = fmaf(-f, zv[q], zk[i]);
+              }
+            }
+          }
+        }
+        __syncwarp();
       }
       if (t + 1 < r && warp == (t + 1) % LW) form_reflector(t + 1);
       __syncthreads();
     }
-    for (int c = r + warp; c < m; c += LW) {
-      float x[NE];
+    // complement columns c = r .. m-1, four per warp at a time: their dot products
+    // and warp sums interleave, so one reflector costs one reduction latency
+    constexpr int NCW = 4;
+    for (int cb = r + warp; cb < m; cb += NCW * LW) {
+      float x[NCW][NE];
 #pragma unroll
-      for (int q = 0; q < NE; ++q) x[q] = (lane + 32 * q == c) ? 1.f : 0.f;
+      for (int w4 = 0; w4 < NCW; ++w4)
+#pragma unroll
+        for (int q = 0; q < NE; ++q) x[w4][q] = (lane + 32 * q == cb + w4 * LW) ? 1.f : 0.f;
       for (int t = r - 1; t >= 0; --t) {
         const float bt = qbeta[t];
         if (bt == 0.f) continue;
         const float* zc = Zq + t * m;
-        float dt = 0.f;
+        float zv[NE];
 #pragma unroll
         for (int q = 0; q < NE; ++q) {
           const int i = lane + 32 * q;
-          if (i >= t && i < m) dt = fmaf(zc[i], x[q], dt);
+          zv[q] = (i >= t && i < m) ? zc[i] : 0.f;
         }
-        dt = warp_sum(dt) * bt;
+        float dt[NCW];
 #pragma unroll
-        for (int q = 0; q < NE; ++q) {
-          const int i = lane + 32 * q;
-          if (i >= t && i < m) x[q] = fmaf(-dt, zc[i], x[q]);
+        for (int w4 = 0; w4 < NCW; ++w4) {
+          float acc = 0.f;
+#pragma unroll
+          for (int q = 0; q < NE; ++q) acc = fmaf(zv[q], x[w4][q], acc);
+          dt[w4] = acc;
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+          for (int w4 = 0; w4 < NCW; ++w4) dt[w4] += __shfl_xor_sync(0xffffffffu, dt[w4], o);
+#pragma unroll
+        for (int w4 = 0; w4 < NCW; ++w4)
+#pragma unroll
+          for (int q = 0; q < NE; ++q) x[w4][q] = fmaf(-dt[w4] * bt, zv[q], x[w4][q]);
       }
-      float* zk = Zs + (int64_t)c * ldz;
 #pragma unroll
-      for (int q = 0; q < NE; ++q) {
-        const int i = lane + 32 * q;
-        if (i < m) zk[i] = x[q];
+      for (int w4 = 0; w4 < NCW; ++w4) {
+        const int c = cb + w4 * LW;
+        if (c < m) {
+          float* zk = Zs + (int64_t)c * ldz;
+#pragma unroll
+          for (int q = 0; q < NE; ++q) {
+            const int i = lane + 32 * q;
+            if (i < m) zk[i] = x[w4][q];
+          }
+        }
       }
     }
   }
