@@ -57,7 +57,7 @@ def _compare(U, L, Uo, Lo, k=None):
 
 
 def test_apmos_uneven_partitions():
-    # config-4 shape scaled down: 6 row blocks of 2,000-9,000 rows, 64 snapshots,
+    # uneven row blocks (the paper's ranks), scaled down: 6 blocks of 2,000-9,000 rows, 64 snapshots,
     # r1 = r2 = 20.  The spectrum (s_i = 0.85^i, 60 modes, noise 1e-5) puts the
     # local truncation at sigma_20 / sigma_1 ~ 0.04, inside what a Gram-based
     # local SVD of FP32 data resolves (the travelling-wave recipe has only ~15

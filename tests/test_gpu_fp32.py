@@ -72,7 +72,7 @@ def _compare(U, D, Uo, Do, sig_tol=SIG_TOL, ang_tol=ANG_TOL, unit=U32, floor=8.0
     return e.max(), e_ang
 
 
-def test_config1_low_rank_fp32():
+def test_low_rank_fp32():
     # M=4096, K=10, 4 batches of B=25, ff=1, rank-40 data, s_i = 10^(-i/8), noise 1e-8
     A, _, _, _ = synthetic.low_rank(4096, 100, 40, 1e-8, seed=1234)
     bs = [synthetic.to_storage(b, torch.float32) for b in _batches(A, 25)]
@@ -113,8 +113,8 @@ def test_rank_deficient_modes_are_zeroed_and_flagged():
 
 
 def test_travelling_waves_fp32():
-    # config-2 recipe at a 64 x 64 grid: 64 modes, amplitudes j^-1.5, noise 1e-3,
-    # K = 32, B = 64, ff = 0.95
+    # travelling-wave recipe on a 64 x 64 grid: 64 modes, amplitudes j^-1.5,
+    # noise 1e-3, K = 32, B = 64, ff = 0.95
     gen = synthetic.TravellingWaves(64, 64, 64, 1.5, 1e-3, seed=1235)
     bs = [synthetic.to_storage(gen.batch(i, 64), torch.float32) for i in range(4)]
     U, D, _ = _gpu_run(bs, K=32, ff=0.95)

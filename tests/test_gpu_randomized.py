@@ -41,8 +41,8 @@ def _oracle_rsvd(batches, K, ff, p, q, seed):
     return oracle.rsvd_run([b.double().numpy() for b in batches], K, ff, p, q, seed)
 
 
-def test_randomized_c2_recipe():
-    # config-2 recipe (64 travelling-wave modes, amplitudes j^-1.5, noise 1e-3,
+def test_randomized_travelling_waves_64_modes():
+    # travelling-wave recipe (64 modes, amplitudes j^-1.5, noise 1e-3,
     # K = 32, B = 64, ff = 0.95, p = 10, q = 1) on a 128 x 128 grid
     gen = synthetic.TravellingWaves(128, 128, 64, 1.5, 1e-3, seed=1235)
     bs = _f32([gen.batch(i, 64) for i in range(4)])
@@ -101,8 +101,8 @@ def test_randomized_deterministic_and_seeded():
     assert not np.array_equal(D1, D3)  # another sketch, another approximation
 
 
-def test_randomized_tensor_core_c3_shape():
-    # config-3 recipe (256 modes, j^-1.2, noise 1e-4, K = 64, B = 128, BF16) with
+def test_randomized_tensor_core_256_mode_waves():
+    # travelling-wave recipe (256 modes, j^-1.2, noise 1e-4, K = 64, B = 128, BF16) with
     # the range finder (p = 10, q = 1) on a 125 x 256 grid
     gen = synthetic.TravellingWaves(125, 256, 256, 1.2, 1e-4, seed=1236)
     bs = [synthetic.to_storage(gen.batch(i, 128), torch.bfloat16) for i in range(3)]

@@ -39,7 +39,7 @@ def test_tc_gram_matches_householder_R():
     assert err <= 2e-6, f"R rel err {err:.3e}"
 
 
-def test_tc_config1_bf16():
+def test_tc_low_rank_bf16():
     A, _, _, _ = synthetic.low_rank(4096, 100, 40, 1e-8, seed=1234)
     bs = _bf16(_batches(A, 25))
     U, D, info = _gpu_run(bs, K=10, ff=1.0, precision=TC)
@@ -61,9 +61,9 @@ def test_tc_low_rank_shapes(M, K, B, nb, ff):
     _compare(U, D, Uo, Do, sig_tol=1e-4, ang_tol=1e-3, unit=U17)
 
 
-def test_tc_travelling_waves_c3_shape():
-    # config-3 recipe (256 modes, amplitudes j^-1.2, noise 1e-4, K=64, B=128,
-    # BF16 snapshots) on a 125 x 256 grid: M = 32000, a ragged last row tile
+def test_tc_travelling_waves_256_modes():
+    # travelling-wave recipe (256 modes, amplitudes j^-1.2, noise 1e-4, K=64,
+    # B=128, BF16 snapshots) on a 125 x 256 grid: M = 32000, a ragged last row tile
     gen = synthetic.TravellingWaves(125, 256, 256, 1.2, 1e-4, seed=1236)
     bs = _bf16([gen.batch(i, 128) for i in range(3)])
     U, D, info = _gpu_run(bs, K=64, ff=0.95, precision=TC)
@@ -80,8 +80,8 @@ def test_tc_agrees_with_fp32_path():
 
 
 @pytest.fixture(scope="module")
-def c3_recipe_256x512():
-    # config-3 recipe (256 travelling-wave modes, amplitudes j^-1.2, noise 1e-4,
+def waves256_grid256x512():
+    # travelling-wave recipe (256 modes, amplitudes j^-1.2, noise 1e-4,
     # BF16 snapshots, K = 64, B = 128, ff = 0.95) on a 256 x 512 grid, 6 batches
     gen = synthetic.TravellingWaves(256, 512, 256, 1.2, 1e-4, seed=1236)
     bs = _bf16([gen.batch(i, 128) for i in range(6)])
@@ -93,10 +93,10 @@ def c3_recipe_256x512():
     (psvd.PSVD_PREC_BF16_TC, 1e-4, 1e-3),
     (psvd.PSVD_PREC_FP32, 1e-5, 1e-4),
 ])
-def test_c3_recipe_fixed_tolerances(c3_recipe_256x512, precision, sig_tol, ang_tol):
+def test_256_mode_waves_fixed_tolerances(waves256_grid256x512, precision, sig_tol, ang_tol):
     # the stated bars with no conditioning allowance, over the full 64-mode
     # subspace (sigma_64 / sigma_1 = 0.0047, gap 64/65 of 3 %)
-    bs, Uo, Do = c3_recipe_256x512
+    bs, Uo, Do = waves256_grid256x512
     U, D, _ = _gpu_run(bs, K=64, ff=0.95, precision=precision)
     e = np.abs(D - Do) / Do
     assert e.max() <= sig_tol, f"sigma rel err {e.max():.3e}"

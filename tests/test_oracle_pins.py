@@ -115,7 +115,7 @@ def test_stream_ff1_rank_le_K_recovers_closed_form():
 
 
 def test_stream_ff1_K_ge_rank_matches_full_svd():
-    # config-1 structure at M = 500 with K = 40 = rank: equals LAPACK SVD of all data
+    # low-rank structure at M = 500 with K = 40 = rank: equals LAPACK SVD of all data
     A, _, _, _ = synthetic.low_rank(500, 100, 40, 1e-8, seed=12)
     A = A.numpy()
     ref_U, ref_s, _ = np.linalg.svd(A, full_matrices=False)
