@@ -61,7 +61,8 @@ extern "C" {
 typedef enum {
   PSVD_F32 = 0,  /* IEEE binary32 */
   PSVD_BF16 = 1, /* bfloat16 (8-bit exponent, 7-bit fraction) */
-  PSVD_F64 = 2   /* IEEE binary64 (only for the small outputs) */
+  PSVD_F64 = 2   /* IEEE binary64: the small outputs, and snapshots of a
+                    PSVD_PREC_FP64 handle */
 } psvd_dtype;
 
 typedef enum {
@@ -72,7 +73,12 @@ typedef enum {
   /* tcgen05 tensor cores: snapshots in BF16, modes stored as a BF16 hi/lo pair
      (16 significant bits), panel Gram and mode update on the tensor cores with
      FP32 accumulation in tensor memory and an FP64 cross-block reduction. */
-  PSVD_PREC_BF16_TC = 1
+  PSVD_PREC_BF16_TC = 1,
+  /* FP64 CUDA cores: modes stored in FP64, panel Gram and mode update in FP64
+     (snapshots PSVD_F32, PSVD_BF16 or PSVD_F64, widened exactly).  The
+     full-precision reference on the device: FP64 runs at a small fraction of
+     the FP32 rate on this GPU.  No randomized front end (low_rank must be 0). */
+  PSVD_PREC_FP64 = 2
 } psvd_precision;
 
 /* --------------------------------------------------------------- config */
@@ -86,7 +92,8 @@ typedef struct {
   int32_t precision;  /* psvd_precision */
   int32_t low_rank;   /* 1: the SVD of each panel is the randomized low-rank SVD
                          of Sec. 3.3 (range finder Y = P*Omega, Omega Gaussian
-                         n x l, n = k + B); 0: exact.  Any precision. */
+                         n x l, n = k + B); 0: exact.  PSVD_PREC_FP32 or
+                         PSVD_PREC_BF16_TC (PSVD_ERR_UNSUPPORTED with FP64). */
   int32_t oversample; /* p >= 0: the sketch has l = min(K + p, k + B) columns */
   int32_t power_iters;/* q in [0, 16]: power iterations of the range finder */
   uint64_t seed;      /* Philox4x32-10 key of the Gaussian sketches: the sketch of
@@ -98,8 +105,8 @@ typedef struct {
 typedef struct psvd_ctx* psvd_handle;
 
 /* psvd_create: allocates a handle for config *cfg (copied).  Device memory:
- * two M x K mode buffers (FP32, or a BF16 hi/lo pair) plus O(M) staging and
- * O((K+max_batch)^2) workspaces.  *out is set to NULL on failure. */
+ * two M x K mode buffers (FP32, a BF16 hi/lo pair, or FP64) plus O(M) staging
+ * and O((K+max_batch)^2) workspaces.  *out is set to NULL on failure. */
 int psvd_create(psvd_handle* out, const psvd_config* cfg);
 
 /* psvd_destroy: synchronises the handle's stream and frees everything it owns.
@@ -107,7 +114,8 @@ int psvd_create(psvd_handle* out, const psvd_config* cfg);
 void psvd_destroy(psvd_handle h);
 
 /* psvd_initialize: Algorithm 1 steps I1-I2 (Sec. 3.1) on the first batch
- * A0 (M x B, leading dimension lda >= M, dtype PSVD_F32 or PSVD_BF16):
+ * A0 (M x B, leading dimension lda >= M, dtype PSVD_F32 or PSVD_BF16, or
+ * PSVD_F64 on a PSVD_PREC_FP64 handle; the tensor-core path takes PSVD_BF16):
  * QR of A0, SVD of R, U0 = Q U' truncated to k = min(K, B) modes.
  * Implemented as the Gram of A0, its eigen-decomposition, and U0 = A0 V D^-1. */
 int psvd_initialize(psvd_handle h, const void* A0, int64_t lda, int32_t B, int32_t dtype);
@@ -168,8 +176,13 @@ int psvd_parallel_qr_static(const void* P, int64_t ldp, int64_t M, int32_t n, in
                             double* R_out, void* stream);
 
 /* psvd_get_modes: copies the current modes (M x k, FP32; a BF16 hi/lo pair is
- * summed exactly) into U_out (ldu >= M, host or device). */
+ * summed exactly, FP64 modes are rounded) into U_out (ldu >= M, host or device). */
 int psvd_get_modes(psvd_handle h, float* U_out, int64_t ldu);
+
+/* psvd_get_modes_f64: the current modes of a PSVD_PREC_FP64 handle (M x k, FP64)
+ * into U_out (ldu >= M, host or device); PSVD_ERR_UNSUPPORTED for the other
+ * precisions.  Synchronises the handle's stream. */
+int psvd_get_modes_f64(psvd_handle h, double* U_out, int64_t ldu);
 
 /* psvd_get_singular_values: copies the current k singular values (descending,
  * FP64) into s_out (host or device). */
@@ -178,9 +191,10 @@ int psvd_get_singular_values(psvd_handle h, double* s_out);
 /* psvd_num_modes: current mode count k (0 before psvd_initialize), or < 0. */
 int psvd_num_modes(psvd_handle h);
 
-/* psvd_save: writes (config, iteration, k, D, U as FP32, Philox counter) to a
- * binary file; psvd_load recreates a handle from it on the given stream.  A
- * loaded handle continues bit-identically to the one that was saved. */
+/* psvd_save: writes (config, iteration, k, D, U as FP32, Philox counter; the
+ * BF16 hi/lo planes or the FP64 modes of those precisions) to a binary file;
+ * psvd_load recreates a handle from it on the given stream.  A loaded handle
+ * continues bit-identically to the one that was saved. */
 int psvd_save(psvd_handle h, const char* path);
 int psvd_load(psvd_handle* out, const char* path, void* stream);
 

@@ -35,6 +35,8 @@ struct psvd_ctx {
   // tensor-core path: both BF16 planes of the modes, slot-tiled (tc_kernels.cuh)
   __nv_bfloat16* Ut[2] = {nullptr, nullptr};
   int Kp = 0;  // column stride of the tiled planes, roundup(K, 8)
+  // FP64 path: modes in FP64 (double-buffered)
+  double* U64[2] = {nullptr, nullptr};
   double* D[2] = {nullptr, nullptr};
   double* partial = nullptr;
   int64_t partial_cap = 0;  // doubles
@@ -146,6 +148,7 @@ int ensure_partial(psvd_ctx* h, int64_t doubles) {
 }
 
 bool use_tc(const psvd_ctx* h) { return h->cfg.precision == PSVD_PREC_BF16_TC; }
+bool use_f64(const psvd_ctx* h) { return h->cfg.precision == PSVD_PREC_FP64; }
 
 // Starts timing a phase (returns the record index, or -1 when not profiling).
 int prof_begin(psvd_ctx* h, int phase) {
@@ -197,12 +200,17 @@ int panel_gram(psvd_ctx* h, const void* A, int64_t lda, int B, int dtype, int kc
                ? PSVD_ERR_CUDA
                : PSVD_OK;
   }
-  PanelF32 p{h->U[h->cur], h->ldu, kc, A, lda, dtype == PSVD_BF16 ? 1 : 0, h->M, n};
   int nchunk;
   int64_t rpc, pd;
   gram_simt_plan(h->M, n, h->num_sms, &nchunk, &rpc, &pd);
   if (int rc = ensure_partial(h, pd)) return rc;
-  CK(gram_simt_launch(p, nchunk, rpc, h->partial, h->st));
+  if (use_f64(h)) {
+    PanelF64 p{h->U64[h->cur], h->ldu, kc, A, lda, dtype, h->M, n};
+    CK(gram_f64_launch(p, nchunk, rpc, h->partial, h->st));
+  } else {
+    PanelF32 p{h->U[h->cur], h->ldu, kc, A, lda, dtype == PSVD_BF16 ? 1 : 0, h->M, n};
+    CK(gram_simt_launch(p, nchunk, rpc, h->partial, h->st));
+  }
   CK(gram_reduce_launch(h->partial, nchunk, n, kc, D, ff, G, h->w.H, h->w.info, h->st));
   return PSVD_OK;
 }
@@ -242,6 +250,9 @@ int step(psvd_ctx* h, const void* A, int64_t lda, int B, int dtype) {
     int rc = tc_update(h->Ut[h->cur], h->Kp, kc, A, lda, B, dtype, h->M, T, n, k1, w.T3,
                        h->Ut[h->cur ^ 1], h->num_sms, &h->w.info[2], h->st);
     if (rc) return rc;
+  } else if (use_f64(h)) {
+    PanelF64 p{h->U64[h->cur], h->ldu, kc, A, lda, dtype, h->M, n};
+    CK(update_f64_launch(p, w.T64, k1, h->U64[h->cur ^ 1], h->ldu, h->st));
   } else {
     PanelF32 p{h->U[h->cur], h->ldu, kc, A, lda, dtype == PSVD_BF16 ? 1 : 0, h->M, n};
     CK(update_simt_launch(p, T, k1, h->U[h->cur ^ 1], h->ldu, h->st));
@@ -256,8 +267,9 @@ int step(psvd_ctx* h, const void* A, int64_t lda, int B, int dtype) {
 
 int check_batch(psvd_ctx* h, const void* A, int64_t lda, int B, int dtype) {
   if (!A || B < 1 || lda < h->M) return PSVD_ERR_INVALID_ARG;
-  if (dtype != PSVD_F32 && dtype != PSVD_BF16) return PSVD_ERR_INVALID_ARG;
+  if (dtype != PSVD_F32 && dtype != PSVD_BF16 && dtype != PSVD_F64) return PSVD_ERR_INVALID_ARG;
   if (use_tc(h) && dtype != PSVD_BF16) return PSVD_ERR_UNSUPPORTED;
+  if (dtype == PSVD_F64 && !use_f64(h)) return PSVD_ERR_UNSUPPORTED;
   if (B > h->maxB) return PSVD_ERR_SHAPE;
   if (h->M < (int64_t)h->kc + B) return PSVD_ERR_SHAPE;
   return PSVD_OK;
@@ -303,7 +315,8 @@ int psvd_create(psvd_handle* out, const psvd_config* cfg) {
   *out = nullptr;
   if (!cfg || cfg->M < 1 || cfg->K < 1 || cfg->max_batch < 1) return PSVD_ERR_INVALID_ARG;
   if (!(cfg->ff > 0.0 && cfg->ff <= 1.0)) return PSVD_ERR_INVALID_ARG;
-  if (cfg->precision != PSVD_PREC_FP32 && cfg->precision != PSVD_PREC_BF16_TC)
+  if (cfg->precision != PSVD_PREC_FP32 && cfg->precision != PSVD_PREC_BF16_TC &&
+      cfg->precision != PSVD_PREC_FP64)
     return PSVD_ERR_INVALID_ARG;
   if ((int64_t)cfg->K + cfg->max_batch > kMaxN) return PSVD_ERR_SHAPE;
   if (cfg->precision == PSVD_PREC_BF16_TC &&
@@ -312,6 +325,7 @@ int psvd_create(psvd_handle* out, const psvd_config* cfg) {
   if (cfg->low_rank != 0 &&
       (cfg->low_rank != 1 || cfg->oversample < 0 || cfg->power_iters < 0 || cfg->power_iters > 16))
     return PSVD_ERR_INVALID_ARG;
+  if (cfg->low_rank && cfg->precision == PSVD_PREC_FP64) return PSVD_ERR_UNSUPPORTED;
   psvd_ctx* h = new (std::nothrow) psvd_ctx();
   if (!h) return PSVD_ERR_ALLOC;
   h->cfg = *cfg;
@@ -335,6 +349,8 @@ int psvd_create(psvd_handle* out, const psvd_config* cfg) {
   for (int b = 0; b < 2 && !rc; ++b) {
     if (use_tc(h)) {
       rc = dalloc(&h->Ut[b], tc_modes_elems(h->M, h->K));
+    } else if (use_f64(h)) {
+      rc = dalloc(&h->U64[b], ucount);
     } else {
       rc = dalloc(&h->U[b], ucount);
     }
@@ -351,6 +367,7 @@ int psvd_create(psvd_handle* out, const psvd_config* cfg) {
   if (!rc) rc = dalloc(&h->w.Xn, nm * nm);
   if (!rc) rc = dalloc(&h->w.lamJ, nm);
   if (!rc) rc = dalloc(&h->w.T, nm * (size_t)h->K);
+  if (!rc && use_f64(h)) rc = dalloc(&h->w.T64, nm * (size_t)h->K);
   if (!rc) rc = dalloc(&h->w.T3, tc_t3_elems(h->K, h->maxB));
   if (!rc) rc = dalloc(&h->w.info, 4);
   if (!rc) rc = dalloc(&h->w.fs, eig_levels_scratch_floats(h->nmax));
@@ -376,6 +393,8 @@ int psvd_create(psvd_handle* out, const psvd_config* cfg) {
     for (int b = 0; b < 2 && !rc; ++b) {
       if (use_tc(h)) {
         if (cudaMemsetAsync(h->Ut[b], 0, tc_modes_elems(h->M, h->K) * 2, h->st)) rc = PSVD_ERR_CUDA;
+      } else if (use_f64(h)) {
+        if (cudaMemsetAsync(h->U64[b], 0, ucount * 8, h->st)) rc = PSVD_ERR_CUDA;
       } else if (cudaMemsetAsync(h->U[b], 0, ucount * 4, h->st)) {
         rc = PSVD_ERR_CUDA;
       }
@@ -401,6 +420,7 @@ void psvd_destroy(psvd_handle h) {
   for (int b = 0; b < 2; ++b) {
     cudaFree(h->U[b]);
     cudaFree(h->Ut[b]);
+    cudaFree(h->U64[b]);
     cudaFree(h->D[b]);
   }
   cudaFree(h->partial);
@@ -431,6 +451,7 @@ void psvd_destroy(psvd_handle h) {
   cudaFree(h->rw.sgn);
   cudaFree(h->staging);
   cudaFree(h->Uf32_tmp);
+  cudaFree(h->w.T64);
   cudaGetLastError();
   delete h;
 }
@@ -464,13 +485,25 @@ int psvd_get_modes(psvd_handle h, float* U_out, int64_t ldo) {
   if (!h || !U_out || ldo < h->M) return PSVD_ERR_INVALID_ARG;
   if (h->kc == 0) return PSVD_ERR_NOT_INITIALIZED;
   const float* src = h->U[h->cur];
-  if (use_tc(h)) {
+  if (use_tc(h) || use_f64(h)) {
     if (!h->Uf32_tmp && dalloc(&h->Uf32_tmp, (size_t)h->ldu * h->K)) return PSVD_ERR_ALLOC;
-    CK(tc_modes_to_f32(h->Ut[h->cur], h->Kp, h->M, h->kc, h->Uf32_tmp, h->ldu, h->st));
+    if (use_tc(h))
+      CK(tc_modes_to_f32(h->Ut[h->cur], h->Kp, h->M, h->kc, h->Uf32_tmp, h->ldu, h->st));
+    else
+      CK(modes_f64_to_f32_launch(h->U64[h->cur], h->ldu, h->M, h->kc, h->Uf32_tmp, h->ldu, h->st));
     src = h->Uf32_tmp;
   }
   CK(cudaMemcpy2DAsync(U_out, sizeof(float) * ldo, src, sizeof(float) * h->ldu,
                        sizeof(float) * h->M, h->kc, cudaMemcpyDefault, h->st));
+  return collect_status(h);
+}
+
+int psvd_get_modes_f64(psvd_handle h, double* U_out, int64_t ldo) {
+  if (!h || !U_out || ldo < h->M) return PSVD_ERR_INVALID_ARG;
+  if (!use_f64(h)) return PSVD_ERR_UNSUPPORTED;
+  if (h->kc == 0) return PSVD_ERR_NOT_INITIALIZED;
+  CK(cudaMemcpy2DAsync(U_out, sizeof(double) * ldo, h->U64[h->cur], sizeof(double) * h->ldu,
+                       sizeof(double) * h->M, h->kc, cudaMemcpyDefault, h->st));
   return collect_status(h);
 }
 
@@ -491,7 +524,8 @@ int psvd_last_info(psvd_handle h, int32_t* info4) {
 int psvd_parallel_qr(psvd_handle h, const void* P, int64_t ldp, int32_t n, int32_t dtype,
                      double* R_out) {
   if (!h || !P || !R_out || n < 1 || ldp < h->M) return PSVD_ERR_INVALID_ARG;
-  if (dtype != PSVD_F32 && dtype != PSVD_BF16) return PSVD_ERR_INVALID_ARG;
+  if (dtype != PSVD_F32 && dtype != PSVD_BF16 && dtype != PSVD_F64) return PSVD_ERR_INVALID_ARG;
+  if (dtype == PSVD_F64 && !use_f64(h)) return PSVD_ERR_UNSUPPORTED;
   if (n > h->nmax || h->M < n) return PSVD_ERR_SHAPE;
   if (use_tc(h) && dtype != PSVD_BF16) return PSVD_ERR_UNSUPPORTED;
   const void* Pd;
@@ -584,7 +618,9 @@ int psvd_gaussian_sketch(uint64_t seed, uint64_t stream_id, int64_t rows, int64_
 }
 
 // File layout: magic "PSVD0001", psvd_config (stream zeroed), int64 iteration,
-// uint64 sketch counter, int32 kc, pad, kc doubles D, M*kc floats U (ld M).
+// uint64 sketch counter, int32 kc, pad, kc doubles D, M*kc floats U (ld M); then,
+// for a tensor-core handle, the Uh and Ul planes (M*kc BF16 each, ld M), for an
+// FP64 handle M*kc doubles U (ld M).
 int psvd_save(psvd_handle h, const char* path) {
   if (!h || !path) return PSVD_ERR_INVALID_ARG;
   if (h->kc == 0) return PSVD_ERR_NOT_INITIALIZED;
@@ -610,6 +646,15 @@ int psvd_save(psvd_handle h, const char* path) {
             hl[p * nu + (size_t)c * h->M + r] = tiled[tc_mode_index(r, p, c, h->Kp)];
     free(tiled);
   }
+  // FP64 handles keep their FP64 modes: save them too
+  double* u64 = nullptr;
+  if (rc >= 0 && use_f64(h)) {
+    u64 = (double*)malloc(sizeof(double) * (nu ? nu : 1));
+    if (!u64) rc = PSVD_ERR_ALLOC;
+    if (rc >= 0 && cudaMemcpy2D(u64, sizeof(double) * h->M, h->U64[h->cur], sizeof(double) * h->ldu,
+                                sizeof(double) * h->M, h->kc, cudaMemcpyDeviceToHost))
+      rc = PSVD_ERR_CUDA;
+  }
   FILE* f = nullptr;
   if (rc >= 0) f = fopen(path, "wb");
   if (rc >= 0 && !f) rc = PSVD_ERR_IO;
@@ -622,12 +667,14 @@ int psvd_save(psvd_handle h, const char* path) {
               fwrite(&kc, 4, 1, f) == 1 && fwrite(&pad, 4, 1, f) == 1 &&
               fwrite(D, sizeof(double), kc, f) == (size_t)kc && fwrite(U, sizeof(float), nu, f) == nu;
     if (ok && hl) ok = fwrite(hl, 2, 2 * nu, f) == 2 * nu;
+    if (ok && u64) ok = fwrite(u64, sizeof(double), nu, f) == nu;
     if (!ok) rc = PSVD_ERR_IO;
   }
   if (f) fclose(f);
   free(U);
   free(D);
   free(hl);
+  free(u64);
   return rc < 0 ? rc : PSVD_OK;
 }
 
@@ -664,6 +711,11 @@ int psvd_load(psvd_handle* out, const char* path, void* stream) {
     hl = (unsigned short*)malloc(2 * 2 * nu);
     if (!hl || fread(hl, 2, 2 * nu, f) != 2 * nu) rc = PSVD_ERR_IO;
   }
+  double* u64 = nullptr;
+  if (!rc && use_f64(h)) {
+    u64 = (double*)malloc(sizeof(double) * nu);
+    if (!u64 || fread(u64, sizeof(double), nu, f) != nu) rc = PSVD_ERR_IO;
+  }
   fclose(f);
   if (!rc) {
     if (use_tc(h)) {
@@ -680,6 +732,9 @@ int psvd_load(psvd_handle* out, const char* path, void* stream) {
         if (cudaMemcpy(h->Ut[0], tiled, 2 * nt, cudaMemcpyHostToDevice)) rc = PSVD_ERR_CUDA;
         free(tiled);
       }
+    } else if (use_f64(h)) {
+      if (cudaMemcpy2D(h->U64[0], 8 * h->ldu, u64, 8 * c.M, 8 * c.M, kc, cudaMemcpyHostToDevice))
+        rc = PSVD_ERR_CUDA;
     } else if (cudaMemcpy2D(h->U[0], 4 * h->ldu, U, 4 * c.M, 4 * c.M, kc, cudaMemcpyHostToDevice)) {
       rc = PSVD_ERR_CUDA;
     }
@@ -688,6 +743,7 @@ int psvd_load(psvd_handle* out, const char* path, void* stream) {
   free(U);
   free(D);
   free(hl);
+  free(u64);
   if (rc) {
     psvd_destroy(h);
     return rc;

@@ -50,6 +50,29 @@ cudaError_t gram_reduce_launch(const double* partial, int nchunk, int n, int kc,
 cudaError_t update_simt_launch(const PanelF32& p, const float* T, int k1, float* Unew,
                                int64_t ldo, cudaStream_t st);
 
+// ---------------------------------------------------------------- FP64 SIMT path
+// Panel [U | A]: U is M x kc FP64 (ldu), A is M x B (lda) of psvd_dtype a_dtype.
+struct PanelF64 {
+  const double* U;
+  int64_t ldu;
+  int kc;
+  const void* A;
+  int64_t lda;
+  int a_dtype;  // PSVD_F32, PSVD_BF16 or PSVD_F64
+  int64_t M;
+  int n;  // kc + B
+};
+// Partial Grams over row chunks (chunks as gram_simt_plan), FP64 throughout; the
+// partial layout is gram_simt's, so gram_reduce_launch sums them.
+cudaError_t gram_f64_launch(const PanelF64& p, int nchunk, int64_t rows_per_chunk, double* partial,
+                            cudaStream_t st);
+// Unew (M x k1 FP64, ldo) = [U | A] * T (n x k1, FP64, ldt = n).
+cudaError_t update_f64_launch(const PanelF64& p, const double* T, int k1, double* Unew, int64_t ldo,
+                              cudaStream_t st);
+// out (M x k FP32, ldo) = U rounded to FP32.
+cudaError_t modes_f64_to_f32_launch(const double* U, int64_t ldu, int64_t M, int k, float* out,
+                                    int64_t ldo, cudaStream_t st);
+
 // ------------------------------------------------------------- small solve
 // Device-side progress of the level-by-level eigen-solve (small_eig.cu).
 struct LevelState {

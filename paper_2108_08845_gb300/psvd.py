@@ -33,7 +33,7 @@ PSVD_ERR_UNSUPPORTED = -8
 PSVD_ERR_TIMEOUT = -9
 
 PSVD_F32, PSVD_BF16, PSVD_F64 = 0, 1, 2
-PSVD_PREC_FP32, PSVD_PREC_BF16_TC = 0, 1
+PSVD_PREC_FP32, PSVD_PREC_BF16_TC, PSVD_PREC_FP64 = 0, 1, 2
 
 
 class PsvdError(RuntimeError):
@@ -82,6 +82,7 @@ def load(build_if_missing: bool = True):
         lib.psvd_parallel_svd.argtypes = [vp, vp, i64, C.POINTER(C.c_int64), i32, i32, i32, i32,
                                           i32, fp, i64, vp]
         lib.psvd_get_modes.argtypes = [vp, fp, i64]
+        lib.psvd_get_modes_f64.argtypes = [vp, vp, i64]
         lib.psvd_get_singular_values.argtypes = [vp, vp]
         lib.psvd_num_modes.argtypes = [vp]
         lib.psvd_save.argtypes = [vp, C.c_char_p]
@@ -172,17 +173,17 @@ def psvd_destroy(h: int) -> None:
 
 
 def psvd_initialize(h: int, A0) -> int:
-    p, ld, _, B, code, _keep = _mat(A0, "A0")
+    p, ld, _, B, code, _keep = _mat(A0, "A0", allow_f64=True)
     return _check(load().psvd_initialize(h, p, ld, B, code), "psvd_initialize")
 
 
 def psvd_incorporate_data(h: int, A) -> int:
-    p, ld, _, B, code, _keep = _mat(A, "A")
+    p, ld, _, B, code, _keep = _mat(A, "A", allow_f64=True)
     return _check(load().psvd_incorporate_data(h, p, ld, B, code), "psvd_incorporate_data")
 
 
 def psvd_parallel_qr(h: int, P, R_out) -> int:
-    p, ld, _, n, code, _keep = _mat(P, "P")
+    p, ld, _, n, code, _keep = _mat(P, "P", allow_f64=True)
     r, _, rr, rc_, rcode, _keep2 = _mat(R_out, "R_out", allow_f64=True)
     if rcode != PSVD_F64 or rr != n or rc_ != n:
         raise ValueError("R_out: must be an n x n float64 matrix")
@@ -218,6 +219,13 @@ def psvd_get_modes(h: int, U_out) -> int:
     if code != PSVD_F32:
         raise ValueError("U_out must be float32")
     return _check(load().psvd_get_modes(h, p, ld), "psvd_get_modes")
+
+
+def psvd_get_modes_f64(h: int, U_out) -> int:
+    p, ld, _, _, code, _keep = _mat(U_out, "U_out", allow_f64=True)
+    if code != PSVD_F64:
+        raise ValueError("U_out must be float64")
+    return _check(load().psvd_get_modes_f64(h, p, ld), "psvd_get_modes_f64")
 
 
 def psvd_get_singular_values(h: int, s_out) -> int:
@@ -273,7 +281,7 @@ class StreamingSVD:
 
     def __init__(self, M, K, max_batch, ff=1.0, precision=PSVD_PREC_FP32, low_rank=0,
                  oversample=10, power_iters=0, seed=0, stream=None):
-        self.M, self.K = int(M), int(K)
+        self.M, self.K, self.precision = int(M), int(K), int(precision)
         self.h = psvd_create(M, K, max_batch, ff, precision, low_rank, oversample, power_iters,
                              seed, stream)
 
@@ -288,10 +296,15 @@ class StreamingSVD:
         return psvd_num_modes(self.h)
 
     def modes(self, device="cuda"):
+        """Current modes, column-major: float64 for a PSVD_PREC_FP64 handle, else float32."""
         import torch
         k = self.num_modes
-        U = torch.empty((k, self.M), dtype=torch.float32, device=device).T
-        psvd_get_modes(self.h, U)
+        if self.precision == PSVD_PREC_FP64:
+            U = torch.empty((k, self.M), dtype=torch.float64, device=device).T
+            psvd_get_modes_f64(self.h, U)
+        else:
+            U = torch.empty((k, self.M), dtype=torch.float32, device=device).T
+            psvd_get_modes(self.h, U)
         return U
 
     def singular_values(self, device="cuda"):
