@@ -240,8 +240,10 @@ int step(psvd_ctx* h, const void* A, int64_t lda, int B, int dtype) {
                                h->cfg.seed, (uint64_t)h->iteration, h->st, &nl));
     T = h->rw.Tupd;
   } else {
-    CK(small_solve_launch(w, n, kc, k1, Dcur, h->cfg.ff, /*refine_steps=*/3, kMaxLevels,
-                          h->st, &nl));
+    // an FP64 Gram resolves eigenvalues down to ~1e-13 lambda_max: up to six
+    // levels of three decades each reach them
+    CK(small_solve_launch(w, n, kc, k1, Dcur, h->cfg.ff, /*refine_steps=*/3,
+                          use_f64(h) ? 6 : kMaxLevels, h->st, &nl));
   }
   prof_end(h, pr);
   h->launches += nl;
@@ -368,6 +370,8 @@ int psvd_create(psvd_handle* out, const psvd_config* cfg) {
   if (!rc) rc = dalloc(&h->w.lamJ, nm);
   if (!rc) rc = dalloc(&h->w.T, nm * (size_t)h->K);
   if (!rc && use_f64(h)) rc = dalloc(&h->w.T64, nm * (size_t)h->K);
+  // Gram resolution: FP64 sums over M rows keep ~u64 sqrt(M) of lambda_max
+  h->w.lam_floor = use_f64(h) ? 1e-13 : 0.0;
   if (!rc) rc = dalloc(&h->w.T3, tc_t3_elems(h->K, h->maxB));
   if (!rc) rc = dalloc(&h->w.info, 4);
   if (!rc) rc = dalloc(&h->w.fs, eig_levels_scratch_floats(h->nmax));

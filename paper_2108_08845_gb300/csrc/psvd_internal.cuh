@@ -103,7 +103,14 @@ struct SmallWork {
   LevelState* ls; // level-solve progress
   float* fs;      // FP32 scratch of the level solve (eig_levels_scratch_floats)
   double* T64;    // optional (may be null): n x K FP64 copy of T
+  // Resolution of the Gram relative to lambda_max: eigenvalues below it are not
+  // resolved (modes zeroed, PSVD_WARN_RANK_DEFICIENT).  0 means 1e-9 (the FP32 and
+  // tensor-core Grams); FP64 Grams resolve far deeper.
+  double lam_floor;
 };
+__host__ __device__ inline double lambda_floor(const SmallWork& w) {
+  return w.lam_floor > 0.0 ? w.lam_floor : 1e-9;
+}
 
 // Eigen-decomposition of H (n x n) and the update coefficients:
 //   H = X diag(lam) X^T (descending), sigma = sqrt(lam[0:k1]),

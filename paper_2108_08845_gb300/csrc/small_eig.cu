@@ -915,7 +915,7 @@ cudaError_t eig_levels_launch(const SmallWork& w, int n, int nJ, int max_levels,
   a.V = w.fs + (size_t)n * n;
   a.vb = w.fs + 2 * (size_t)n * n;
   a.tau = 1e-3;
-  a.floor_rel = 1e-9;
+  a.floor_rel = lambda_floor(w);
   a.ctol = 1e-5;
   int nl = 0;
   level_init_kernel<<<1, 1, 0, st>>>(w.ls);

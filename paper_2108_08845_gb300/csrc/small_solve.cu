@@ -21,11 +21,10 @@ namespace psvd {
 namespace {
 
 // Resolution of a Gram-based factorisation: eigenvalues of the scaled Gram below
-// kLambdaFloor * lambda_max (singular values below sqrt of that times sigma_max)
+// lam_floor * lambda_max (singular values below sqrt of that times sigma_max)
 // are at the rounding level of the Gram and are not resolved; such kept modes
-// are set to zero and reported as PSVD_WARN_RANK_DEFICIENT.
-constexpr double kLambdaFloor = 1e-9;
-constexpr double kSigmaFloor = 3.1622776601683795e-5;  // sqrt(kLambdaFloor)
+// are set to zero and reported as PSVD_WARN_RANK_DEFICIENT.  The floor is the
+// Gram's (lambda_floor(w)): 1e-9 for the FP32 and tensor-core Grams.
 
 // Sort key with a total order: NaN ranks below every number (ties broken by index
 // by the callers), so descending ranks are always a permutation.
@@ -78,17 +77,17 @@ __global__ void __launch_bounds__(64) dgemm_kernel(int m, int nn, int k, double 
 // Jacobi values beyond.  The cluster test is relative, |lt_j - lt_i| <=
 // tau * max(|lt_i|, |lt_j|), since the Jacobi stage is relatively accurate on
 // graded matrices (OA's absolute threshold would merge every small eigenvalue).
-// Eigenpairs below the Gram's resolution (lambda <= kLambdaFloor * lambda_max)
+// Eigenpairs below the Gram's resolution (lambda <= lam_floor * lambda_max)
 // carry no information and are left unrefined (E column zero).
 __global__ void oa_correct_kernel(int n, int nJ, const double* __restrict__ S,
                                   const double* __restrict__ XtX, const double* __restrict__ lam,
-                                  double tau, double* __restrict__ E, double* __restrict__ lamJ,
-                                  int* __restrict__ info) {
+                                  double tau, double lam_floor, double* __restrict__ E,
+                                  double* __restrict__ lamJ, int* __restrict__ info) {
   const int j = blockIdx.x;
   const double* Sj = S + (int64_t)j * n;
   const double* Rj = XtX + (int64_t)j * n;
   const double ltj = Sj[j] / Rj[j];
-  if (!(lam[j] > kLambdaFloor * lam[0])) {
+  if (!(lam[j] > lam_floor * lam[0])) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) E[i + (int64_t)j * n] = 0.0;
     if (threadIdx.x == 0) lamJ[j] = lam[j];
     return;
@@ -150,9 +149,9 @@ __global__ void copy_cols_kernel(const double* __restrict__ src, double* __restr
 // Sort the refined eigenpairs, truncate to k1 and form the update coefficients.
 __global__ void finalize_kernel(int n, int nJ, int kc, int k1, const double* __restrict__ X,
                                 const double* __restrict__ lamJ, const double* __restrict__ D,
-                                double ff, float* __restrict__ T, __nv_bfloat16* __restrict__ T3,
-                                double* __restrict__ T64, double* __restrict__ Dnew,
-                                int* __restrict__ info) {
+                                double ff, double sig_floor, float* __restrict__ T,
+                                __nv_bfloat16* __restrict__ T3, double* __restrict__ T64,
+                                double* __restrict__ Dnew, int* __restrict__ info) {
   __shared__ int order[kMaxN];
   __shared__ double sig[kMaxN], xn[kMaxN];
   const int tid = threadIdx.x;
@@ -183,7 +182,7 @@ __global__ void finalize_kernel(int n, int nJ, int kc, int k1, const double* __r
   const double s0 = sig[0];
   if (tid < k1) {
     double s = sig[tid];
-    if (!(s > kSigmaFloor * s0) || !isfinite(s)) {
+    if (!(s > sig_floor * s0) || !isfinite(s)) {
       if (!isfinite(s) || !isfinite(s0)) atomicOr(&info[2], 4);
       else atomicOr(&info[2], 1);
       s = 0.0;
@@ -278,7 +277,8 @@ cudaError_t small_solve_launch(const SmallWork& w, int n, int kc, int k1, const 
     if ((e = dgemm<false>(n, nJ, n, 1.0, w.H, n, w.X, n, 0.0, nullptr, n, w.W, n, st))) return e;
     if ((e = dgemm<true>(n, nJ, n, 1.0, w.X, n, w.W, n, 0.0, nullptr, n, w.S, n, st))) return e;
     if ((e = dgemm<true>(n, nJ, n, 1.0, w.X, n, w.X, n, 0.0, nullptr, n, w.R, n, st))) return e;
-    oa_correct_kernel<<<nJ, 256, 0, st>>>(n, nJ, w.S, w.R, w.lam, 1e-5, w.E, w.lamJ, w.info);
+    oa_correct_kernel<<<nJ, 256, 0, st>>>(n, nJ, w.S, w.R, w.lam, 1e-5, lambda_floor(w), w.E,
+                                          w.lamJ, w.info);
     if ((e = cudaGetLastError())) return e;
     // X_J <- X_J + X E
     if ((e = dgemm<false>(n, nJ, n, 1.0, w.X, n, w.E, n, 1.0, w.X, n, w.Xn, n, st))) return e;
@@ -291,8 +291,8 @@ cudaError_t small_solve_launch(const SmallWork& w, int n, int kc, int k1, const 
   if ((e = dgemm<false>(n, nJ, n, 1.0, w.H, n, w.X, n, 0.0, nullptr, n, w.W, n, st))) return e;
   rayleigh_kernel<<<nJ, 256, 0, st>>>(n, nJ, w.X, w.W, w.lamJ);
   if ((e = cudaGetLastError())) return e;
-  finalize_kernel<<<1, 256, 0, st>>>(n, nJ, kc, k1, w.X, w.lamJ, D, ff, w.T, nullptr, w.T64, w.Dnew,
-                                    w.info);
+  finalize_kernel<<<1, 256, 0, st>>>(n, nJ, kc, k1, w.X, w.lamJ, D, ff, sqrt(lambda_floor(w)), w.T,
+                                    nullptr, w.T64, w.Dnew, w.info);
   *launches = nl + 1 + 6 * refine_steps + 3;
   return cudaGetLastError();
 }
