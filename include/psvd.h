@@ -145,8 +145,12 @@ int psvd_parallel_qr(psvd_handle h, const void* P, int64_t ldp, int32_t n, int32
  * Outputs: U_out (Mtot x r2, FP32, ldu >= Mtot), L_out (r2, FP64, descending),
  * host or device.  N <= 192, r1 <= N, r2 <= min(N, r1*nparts).  Runs on the
  * FP32 path for either handle precision and uses the handle only for its
- * stream and staging buffer; workspace is allocated and freed by the call,
- * which synchronises the stream.  Returns PSVD_WARN_RANK_DEFICIENT when a kept
+ * stream and staging buffer; its workspaces (one per concurrent lane: the
+ * blocks' local solves run on up to 16 streams of the handle's own) are kept
+ * by the handle after the first call and grown when a call needs more.  The
+ * launch sequence is captured into a CUDA graph on the first call with a given
+ * argument set and replayed by later calls with the same pointers and sizes.
+ * The call synchronises the stream.  Returns PSVD_WARN_RANK_DEFICIENT when a kept
  * L~_j is numerically zero (that mode is returned as zero). */
 int psvd_parallel_svd(psvd_handle h, const void* A, int64_t lda, const int64_t* part_offsets,
                       int32_t nparts, int32_t N, int32_t dtype, int32_t r1, int32_t r2,

@@ -8,8 +8,14 @@
 //     eigenvectors are the left singular vectors X~ of W and whose eigenvalues
 //     are L~^2;
 //   U~ = A X~ diag(1/L~) over all rows at once (the same T = X~ diag(1/L~)).
+// The local solves are latency-bound chains (the eigen-solve's level kernel runs
+// on one SM), so the blocks run concurrently: up to kLanes streams, each with its
+// own workspace, take the blocks round-robin; every block writes its factors to
+// its own slot, and W W^T sums the slots in block order after the join, so the
+// result does not depend on which lane finished first.
 #include <stdint.h>
 
+#include <new>
 #include <vector>
 
 #include "psvd_internal.cuh"
@@ -17,64 +23,109 @@
 namespace psvd {
 namespace {
 
-// WW += Vs Vs^T with Vs = T64[:, 0:r1] diag(sigma^2) (N x N, FP64).
-__global__ void wwt_accumulate_kernel(int N, int r1, const double* __restrict__ T64,
-                                      const double* __restrict__ sigma, double* __restrict__ WW) {
+constexpr int kLanes = 16;
+
+// WW = sum_b Vs_b Vs_b^T, blocks in order, with Vs_b = T64_b[:, 0:r1] diag(sigma_b^2)
+// (T64_b: N x r1 FP64 at T64 + b * N * r1, sigma_b at sigma + b * r1).
+__global__ void wwt_kernel(int N, int r1, int nparts, const double* __restrict__ T64,
+                           const double* __restrict__ sigma, double* __restrict__ WW) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= N * N) return;
   const int i = e % N, j = e / N;
   double acc = 0.0;
-  for (int k = 0; k < r1; ++k) {
-    const double s2 = sigma[k] * sigma[k];
-    acc = fma(T64[i + (int64_t)k * N] * s2, T64[j + (int64_t)k * N] * s2, acc);
+  for (int b = 0; b < nparts; ++b) {
+    const double* Tb = T64 + (size_t)b * N * r1;
+    const double* sb = sigma + (size_t)b * r1;
+    for (int k = 0; k < r1; ++k) {
+      const double s2 = sb[k] * sb[k];
+      acc = fma(Tb[i + (int64_t)k * N] * s2, Tb[j + (int64_t)k * N] * s2, acc);
+    }
   }
-  WW[e] += acc;
+  WW[e] = acc;
 }
 
-struct Buffers {
-  std::vector<void*> ptrs;
-  bool failed = false;
-  ~Buffers() {
-    for (void* p : ptrs) cudaFree(p);
-  }
-  template <typename T>
-  T* get(size_t count) {
-    void* p = nullptr;
-    if (cudaMalloc(&p, sizeof(T) * (count ? count : 1)) != cudaSuccess) {
+// OR of the lanes' status words into info[2].
+__global__ void merge_info_kernel(const int* __restrict__ lane_info, int nlanes, int* __restrict__ info) {
+  int bits = 0;
+  for (int l = 0; l < nlanes; ++l) bits |= lane_info[4 * l + 2];
+  info[2] |= bits;
+}
+
+// Device buffer that grows on demand (contents are not kept across growth).
+template <typename T>
+struct Grow {
+  T* p = nullptr;
+  size_t cap = 0;
+  bool ensure(size_t count) {
+    if (count == 0) count = 1;
+    if (count <= cap) return true;
+    cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    if (cudaMalloc((void**)&p, sizeof(T) * count) != cudaSuccess) {
       cudaGetLastError();
-      failed = true;
-      return nullptr;
+      return false;
     }
-    ptrs.push_back(p);
-    return static_cast<T*>(p);
+    cap = count;
+    return true;
   }
+  ~Grow() { cudaFree(p); }
+};
+
+struct Lane {
+  Grow<double> H, X, lam, W, S, R, E, Xn, lamJ, T64, Dnew, partial;
+  Grow<float> T, fs;
+  Grow<LevelState> ls;
+  cudaStream_t st = nullptr;
+  cudaEvent_t done = nullptr;
 };
 
 }  // namespace
 
+// Workspaces and streams of apmos_run, kept by the handle across calls so that a
+// call only enqueues work (no allocation once the sizes have been seen).
+// The launch sequence of a call (thousands of small kernels: the local solves are
+// chains of ~45 launches each) is captured into a CUDA graph; a later call with
+// the same arguments and buffers replays it with one launch.
+struct ApmosCache {
+  Lane lane[kLanes];
+  Grow<int> lane_info;
+  Grow<double> T64_all, S_all, WW;
+  cudaEvent_t fork = nullptr;
+  // the sequence is captured and replayed on this stream (capture cannot start
+  // on the legacy default stream); it is ordered after and before the caller's
+  cudaStream_t origin = nullptr;
+  cudaEvent_t in = nullptr, out = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<int64_t> key;  // arguments and buffer addresses the graph was captured with
+  ~ApmosCache() {
+    if (exec) cudaGraphExecDestroy(exec);
+    for (Lane& l : lane) {
+      if (l.st) cudaStreamDestroy(l.st);
+      if (l.done) cudaEventDestroy(l.done);
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (origin) cudaStreamDestroy(origin);
+    if (in) cudaEventDestroy(in);
+    if (out) cudaEventDestroy(out);
+  }
+};
+
+ApmosCache* apmos_cache_create() { return new (std::nothrow) ApmosCache(); }
+
+int apmos_enqueue(ApmosCache* c, const std::vector<SmallWork>& lw, int nlanes, const void* A,
+                  size_t es, int64_t lda, int a_bf16, int64_t Mtot, const int64_t* off, int nparts,
+                  int N, int r1, int r2, float* U, int64_t ldu, double* L, int num_sms,
+                  cudaStream_t st);
+void apmos_cache_destroy(ApmosCache* c) { delete c; }
+
 int apmos_run(const void* A, int64_t lda, int a_bf16, int64_t Mtot, const int64_t* off, int nparts,
               int N, int r1, int r2, float* U, int64_t ldu, double* L, int num_sms,
-              cudaStream_t st, int* status) {
+              cudaStream_t st, ApmosCache* c, int* status) {
+  if (!c) return PSVD_ERR_INVALID_ARG;
   const size_t es = a_bf16 ? 2 : 4;
   const size_t nn = (size_t)N * N;
-  Buffers buf;
-  SmallWork w{};
-  w.H = buf.get<double>(nn);
-  w.X = buf.get<double>(nn);
-  w.lam = buf.get<double>(N);
-  w.W = buf.get<double>(nn);
-  w.S = buf.get<double>(nn);
-  w.R = buf.get<double>(nn);
-  w.E = buf.get<double>(nn);
-  w.Xn = buf.get<double>(nn);
-  w.lamJ = buf.get<double>(N);
-  w.T = buf.get<float>(nn);
-  w.T64 = buf.get<double>(nn);
-  w.Dnew = buf.get<double>(N);
-  w.info = buf.get<int>(4);
-  w.ls = buf.get<LevelState>(1);
-  w.fs = buf.get<float>(eig_levels_scratch_floats(N));
-  double* WW = buf.get<double>(nn);
+  const int nlanes = nparts < kLanes ? nparts : kLanes;
   int64_t pmax = 0;
   for (int b = 0; b < nparts; ++b) {
     int nchunk;
@@ -82,41 +133,160 @@ int apmos_run(const void* A, int64_t lda, int a_bf16, int64_t Mtot, const int64_
     gram_simt_plan(off[b + 1] - off[b], N, num_sms, &nchunk, &rpc, &pd);
     if (pd > pmax) pmax = pd;
   }
-  double* partial = buf.get<double>((size_t)pmax);
-  if (buf.failed) return PSVD_ERR_ALLOC;
-#define ACK(x)                                     \
-  do {                                             \
-    if ((x) != cudaSuccess) return PSVD_ERR_CUDA;  \
+  // growing a buffer frees the old one: nothing may still be using it
+  if (cudaStreamSynchronize(st) != cudaSuccess) return PSVD_ERR_CUDA;
+  bool ok = c->lane_info.ensure(4 * (size_t)nlanes) && c->T64_all.ensure((size_t)nparts * N * r1) &&
+            c->S_all.ensure((size_t)nparts * r1) && c->WW.ensure(nn);
+  std::vector<SmallWork> lw(nlanes);
+  for (int l = 0; l < nlanes && ok; ++l) {
+    Lane& ln = c->lane[l];
+    ok = ln.H.ensure(nn) && ln.X.ensure(nn) && ln.lam.ensure(N) && ln.W.ensure(nn) &&
+         ln.S.ensure(nn) && ln.R.ensure(nn) && ln.E.ensure(nn) && ln.Xn.ensure(nn) &&
+         ln.lamJ.ensure(N) && ln.T.ensure(nn) && ln.T64.ensure(nn) && ln.Dnew.ensure(N) &&
+         ln.ls.ensure(1) && ln.fs.ensure(eig_levels_scratch_floats(N)) &&
+         ln.partial.ensure((size_t)pmax);
+    if (ok && !ln.st) ok = cudaStreamCreateWithFlags(&ln.st, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok && !ln.done) ok = cudaEventCreateWithFlags(&ln.done, cudaEventDisableTiming) == cudaSuccess;
+    SmallWork& w = lw[l];
+    w = SmallWork{};
+    w.H = ln.H.p;
+    w.X = ln.X.p;
+    w.lam = ln.lam.p;
+    w.W = ln.W.p;
+    w.S = ln.S.p;
+    w.R = ln.R.p;
+    w.E = ln.E.p;
+    w.Xn = ln.Xn.p;
+    w.lamJ = ln.lamJ.p;
+    w.T = ln.T.p;
+    w.T64 = ln.T64.p;
+    w.Dnew = ln.Dnew.p;
+    w.info = c->lane_info.p + 4 * l;
+    w.ls = ln.ls.p;
+    w.fs = ln.fs.p;
+  }
+  if (ok && !c->fork) ok = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) == cudaSuccess;
+  if (ok && !c->origin) ok = cudaStreamCreateWithFlags(&c->origin, cudaStreamNonBlocking) == cudaSuccess;
+  if (ok && !c->in) ok = cudaEventCreateWithFlags(&c->in, cudaEventDisableTiming) == cudaSuccess;
+  if (ok && !c->out) ok = cudaEventCreateWithFlags(&c->out, cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    return PSVD_ERR_ALLOC;
+  }
+#define ACK(x)                                    \
+  do {                                            \
+    if ((x) != cudaSuccess) {                     \
+      cudaGetLastError();                         \
+      return PSVD_ERR_CUDA;                       \
+    }                                             \
   } while (0)
-  ACK(cudaMemsetAsync(w.info, 0, sizeof(int) * 4, st));
-  ACK(cudaMemsetAsync(WW, 0, sizeof(double) * nn, st));
+  int* lane_info = c->lane_info.p;
+  double* T64_all = c->T64_all.p;  // block b's N x r1 factor
+  double* WW = c->WW.p;
+  std::vector<int64_t> key = {(int64_t)(uintptr_t)A, lda, a_bf16, Mtot, nparts, N, r1, r2,
+                              (int64_t)(uintptr_t)U, ldu, (int64_t)(uintptr_t)L, num_sms,
+                              (int64_t)(uintptr_t)st, (int64_t)(uintptr_t)lane_info,
+                              (int64_t)(uintptr_t)T64_all, (int64_t)(uintptr_t)WW};
+  for (int b = 0; b <= nparts; ++b) key.push_back(off[b]);
+  for (int l = 0; l < nlanes; ++l) key.push_back((int64_t)(uintptr_t)c->lane[l].partial.p);
+  // origin runs after the work already on st
+  cudaStream_t o = c->origin;
+  ACK(cudaEventRecord(c->in, st));
+  ACK(cudaStreamWaitEvent(o, c->in, 0));
+  if (!(c->exec && key == c->key)) {
+    if (c->exec) {
+      cudaGraphExecDestroy(c->exec);
+      c->exec = nullptr;
+    }
+    c->key.clear();
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(o, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+      const int rc = apmos_enqueue(c, lw, nlanes, A, es, lda, a_bf16, Mtot, off, nparts, N, r1, r2,
+                                   U, ldu, L, num_sms, o);
+      const cudaError_t ec = cudaStreamEndCapture(o, &graph);
+      if (rc == PSVD_OK && ec == cudaSuccess && graph &&
+          cudaGraphInstantiate(&c->exec, graph, 0) == cudaSuccess)
+        c->key = key;
+      else
+        c->exec = nullptr;
+      if (graph) cudaGraphDestroy(graph);
+    }
+    cudaGetLastError();
+  }
+  if (c->exec) {
+    ACK(cudaGraphLaunch(c->exec, o));
+  } else {
+    // no graph (capture unavailable): enqueue the sequence directly
+    if (int rc = apmos_enqueue(c, lw, nlanes, A, es, lda, a_bf16, Mtot, off, nparts, N, r1, r2, U,
+                               ldu, L, num_sms, o))
+      return rc;
+  }
+  ACK(cudaEventRecord(c->out, o));
+  ACK(cudaStreamWaitEvent(st, c->out, 0));
+  int info[4] = {0, 0, 0, 0};
+  ACK(cudaMemcpyAsync(info, lane_info, sizeof(info), cudaMemcpyDeviceToHost, st));
+  ACK(cudaStreamSynchronize(st));
+#undef ACK
+  *status = info[2];
+  return PSVD_OK;
+}
+
+// Enqueues one APMOS run on st and the lanes' streams (captured by the caller).
+int apmos_enqueue(ApmosCache* c, const std::vector<SmallWork>& lw, int nlanes, const void* A,
+                  size_t es, int64_t lda, int a_bf16, int64_t Mtot, const int64_t* off, int nparts,
+                  int N, int r1, int r2, float* U, int64_t ldu, double* L, int num_sms,
+                  cudaStream_t st) {
+#define ACK(x)                  \
+  do {                          \
+    if ((x) != cudaSuccess) {   \
+      cudaGetLastError();       \
+      return PSVD_ERR_CUDA;     \
+    }                           \
+  } while (0)
+  const size_t nn = (size_t)N * N;
+  int* lane_info = c->lane_info.p;
+  double* T64_all = c->T64_all.p;
+  double* S_all = c->S_all.p;
+  double* WW = c->WW.p;
+  ACK(cudaMemsetAsync(lane_info, 0, sizeof(int) * 4 * nlanes, st));
+  // fork: every lane starts after the work already on st
+  ACK(cudaEventRecord(c->fork, st));
+  for (int l = 0; l < nlanes; ++l) ACK(cudaStreamWaitEvent(c->lane[l].st, c->fork, 0));
   int nl = 0;
   for (int b = 0; b < nparts; ++b) {
-    // local block: Gram, eigen-decomposition, W_b W_b^T
+    // local block: Gram, eigen-decomposition, factor V~ S~ into slot b
+    const int l = b % nlanes;
+    Lane& ln = c->lane[l];
+    SmallWork w = lw[l];
+    w.T64 = T64_all + (size_t)b * N * r1;
+    w.Dnew = S_all + (size_t)b * r1;
     const int64_t mb = off[b + 1] - off[b];
     const void* Ab = static_cast<const char*>(A) + (size_t)off[b] * es;
     PanelF32 p{nullptr, 0, 0, Ab, lda, a_bf16, mb, N};
     int nchunk;
     int64_t rpc, pd;
     gram_simt_plan(mb, N, num_sms, &nchunk, &rpc, &pd);
-    ACK(gram_simt_launch(p, nchunk, rpc, partial, st));
-    ACK(gram_reduce_launch(partial, nchunk, N, 0, nullptr, 1.0, nullptr, w.H, w.info, st));
-    ACK(small_solve_launch(w, N, 0, r1, nullptr, 1.0, 3, kMaxLevels, st, &nl));
-    wwt_accumulate_kernel<<<(unsigned)ceil_div((int64_t)nn, 256), 256, 0, st>>>(N, r1, w.T64,
-                                                                              w.Dnew, WW);
-    ACK(cudaGetLastError());
+    ACK(gram_simt_launch(p, nchunk, rpc, ln.partial.p, ln.st));
+    ACK(gram_reduce_launch(ln.partial.p, nchunk, N, 0, nullptr, 1.0, nullptr, w.H, w.info, ln.st));
+    ACK(small_solve_launch(w, N, 0, r1, nullptr, 1.0, 3, kMaxLevels, ln.st, &nl));
   }
+  // join, then W W^T in block order
+  for (int l = 0; l < nlanes; ++l) {
+    ACK(cudaEventRecord(c->lane[l].done, c->lane[l].st));
+    ACK(cudaStreamWaitEvent(st, c->lane[l].done, 0));
+  }
+  SmallWork w = lw[0];
+  wwt_kernel<<<(unsigned)ceil_div((int64_t)nn, 256), 256, 0, st>>>(N, r1, nparts, T64_all, S_all, WW);
+  ACK(cudaGetLastError());
+  merge_info_kernel<<<1, 1, 0, st>>>(lane_info, nlanes, lane_info);
+  ACK(cudaGetLastError());
   // global: eigen-decomposition of W W^T, T = X~ diag(1/L~), U = A T
   ACK(cudaMemcpyAsync(w.H, WW, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st));
   ACK(small_solve_launch(w, N, 0, r2, nullptr, 1.0, 3, kMaxLevels, st, &nl));
   PanelF32 pa{nullptr, 0, 0, A, lda, a_bf16, Mtot, N};
   ACK(update_simt_launch(pa, w.T, r2, U, ldu, st));
   ACK(cudaMemcpyAsync(L, w.Dnew, sizeof(double) * r2, cudaMemcpyDeviceToDevice, st));
-  int info[4] = {0, 0, 0, 0};
-  ACK(cudaMemcpyAsync(info, w.info, sizeof(info), cudaMemcpyDeviceToHost, st));
-  ACK(cudaStreamSynchronize(st));
 #undef ACK
-  *status = info[2];
   return PSVD_OK;
 }
 

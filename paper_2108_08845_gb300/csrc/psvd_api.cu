@@ -47,6 +47,7 @@ struct psvd_ctx {
   void* staging = nullptr;
   size_t staging_bytes = 0;
   float* Uf32_tmp = nullptr;  // FP32 view of hi/lo modes for get_modes / save
+  ApmosCache* apmos = nullptr;  // psvd_parallel_svd workspaces and streams (lazily made)
   int host_info[4] = {0, 0, 0, 0};
   int sticky_status = 0;
   // per-phase event timing (psvd_set_profiling)
@@ -455,6 +456,7 @@ void psvd_destroy(psvd_handle h) {
   cudaFree(h->rw.sgn);
   cudaFree(h->staging);
   cudaFree(h->Uf32_tmp);
+  apmos_cache_destroy(h->apmos);
   cudaFree(h->w.T64);
   cudaGetLastError();
   delete h;
@@ -574,8 +576,10 @@ int psvd_parallel_svd(psvd_handle h, const void* A, int64_t lda, const int64_t* 
     return PSVD_ERR_ALLOC;
   }
   int bits = 0;
-  int rc = apmos_run(Ad, ldd, dtype == PSVD_BF16 ? 1 : 0, Mtot, part_offsets, nparts, N, r1, r2,
-                     Ud, ldud, Ld, h->num_sms, h->st, &bits);
+  if (!h->apmos) h->apmos = apmos_cache_create();
+  int rc = h->apmos ? apmos_run(Ad, ldd, dtype == PSVD_BF16 ? 1 : 0, Mtot, part_offsets, nparts, N,
+                                r1, r2, Ud, ldud, Ld, h->num_sms, h->st, h->apmos, &bits)
+                    : PSVD_ERR_ALLOC;
   if (rc == PSVD_OK && !u_dev &&
       cudaMemcpy2DAsync(U_out, sizeof(float) * ldu, Ud, sizeof(float) * ldud, sizeof(float) * Mtot,
                         r2, cudaMemcpyDeviceToHost, h->st) != cudaSuccess)

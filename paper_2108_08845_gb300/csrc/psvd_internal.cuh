@@ -164,9 +164,12 @@ cudaError_t randomized_solve_launch(const RandWork& r, const SmallWork& w, int n
 // FP32, ldu) and L (r2, FP64) on the device.  *status receives the accumulated
 // status bits (1 rank deficient, 4 non-finite).  Allocates and frees its own
 // workspace; synchronises the stream.
+struct ApmosCache;
+ApmosCache* apmos_cache_create();
+void apmos_cache_destroy(ApmosCache* c);
 int apmos_run(const void* A, int64_t lda, int a_bf16, int64_t Mtot, const int64_t* off, int nparts,
               int N, int r1, int r2, float* U, int64_t ldu, double* L, int num_sms,
-              cudaStream_t st, int* status);
+              cudaStream_t st, ApmosCache* cache, int* status);
 
 // -------------------------------------------------------------------- Philox
 cudaError_t gaussian_sketch_launch(uint64_t seed, uint64_t stream_id, int64_t rows, int64_t cols,

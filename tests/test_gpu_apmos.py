@@ -126,3 +126,20 @@ def test_apmos_argument_errors(sizes, r1, r2, status):
     with pytest.raises(psvd.PsvdError) as ei:
         _gpu_apmos(A, _offsets(sizes), r1, r2)
     assert ei.value.status == status
+
+
+def test_apmos_many_partitions_concurrent_lanes():
+    # 40 uneven row blocks: more blocks than concurrent lanes, so every lane takes
+    # several; the result must not depend on the lanes' timing (fixed-order gather)
+    rng = np.random.default_rng(4242)
+    sizes = rng.integers(1000, 4001, size=40)
+    A64, _, _, _ = synthetic.low_rank(int(sizes.sum()), 48, 40, 1e-5, seed=4242,
+                                      s=[0.85 ** i for i in range(40)])
+    A = synthetic.to_storage(A64, torch.float32)
+    off = _offsets(sizes)
+    U1, L1, rc = _gpu_apmos(A, off, 16, 12)
+    U2, L2, _ = _gpu_apmos(A, off, 16, 12)
+    assert rc in (psvd.PSVD_OK, psvd.PSVD_WARN_RANK_DEFICIENT)
+    assert np.array_equal(U1, U2) and np.array_equal(L1, L2)
+    Uo, Lo = oracle.apmos(A.double().numpy(), off, 16, 12)
+    _compare(U1, L1, Uo, Lo, k=10)
