@@ -46,6 +46,10 @@ extern "C" {
                                         its mode is set to zero (Alg. 2, Lambda_j = 0) */
 #define PSVD_WARN_NOT_CONVERGED 2    /* the small Jacobi eigen-solve hit its sweep cap;
                                         results are those of the last sweep */
+#define PSVD_WARN_DEGENERATE 3       /* psvd_update_adjoint: two kept singular values, or
+                                        the last kept and the first dropped one, coincide
+                                        (to 1e-13 relative in s^2); the derivative is
+                                        undefined and the returned one is not meaningful */
 #define PSVD_ERR_INVALID_ARG -1      /* null handle/pointer, ld < M, bad enum, ff not in (0,1] */
 #define PSVD_ERR_NOT_INITIALIZED -2  /* psvd_incorporate_data / get before psvd_initialize */
 #define PSVD_ERR_SHAPE -3            /* B > max_batch, M < K + B, K + max_batch > 192, ... */
@@ -209,6 +213,36 @@ int psvd_load(psvd_handle* out, const char* path, void* stream);
  * to FP32.  Enqueued on `stream` (cudaStream_t, NULL = default). */
 int psvd_gaussian_sketch(uint64_t seed, uint64_t stream_id, int64_t rows, int64_t cols,
                          float* out, void* stream);
+
+/* Adjoint (reverse-mode derivative) of one step of Algorithm 1 (Sec. 3.1, steps 1-5),
+ * or of the initialisation I1-I2 when kc = 0: the hand-written backward of the
+ * panel factorisation and truncated SVD of R, with the 1/(s_i^2 - s_j^2) terms.
+ *
+ * The forward step maps P = [ff U diag(D) | A] (M x n, n = kc + B; P = A when
+ * kc = 0) to its leading k1 left singular vectors U_new and singular values D_new
+ * (what psvd_initialize / psvd_incorporate_data computed, read back with
+ * psvd_get_modes / psvd_get_singular_values).  Given the cotangents U_new_bar
+ * (M x k1) and D_new_bar (k1) of a scalar loss, this returns the cotangents of the
+ * step's inputs:  U_bar (M x kc), D_bar (kc) and A_bar (M x B).  Q is not kept:
+ * the right singular vectors are recovered from U_new (V_k = P^T U_new / D_new) and
+ * the dropped directions enter through shifted FP64 solves on the (n x n) Gram, so
+ * a sweep over a run needs only the per-step modes and singular values.
+ *
+ * Arguments: M and ff are the handle's; U (FP32, ldu), A (dtype PSVD_F32 or
+ * PSVD_BF16, lda), U_new, U_new_bar (FP32) and the outputs U_bar, A_bar (FP32) are
+ * DEVICE pointers with leading dimensions >= M; D, D_new, D_new_bar, D_bar (FP64)
+ * may be host or device.  U, D, U_bar, D_bar may be null when kc = 0.
+ * kc + B <= 192, 1 <= k1 <= min(kc + B, 64), M >= kc + B.  The handle's stream is
+ * used and synchronised; workspaces are kept by the handle.  Arithmetic: FP32
+ * panel passes (float-float row sums, FP64 reduction), FP64 small side.
+ * Returns PSVD_OK, PSVD_WARN_DEGENERATE, PSVD_ERR_NONFINITE, or an argument /
+ * CUDA / allocation error (outputs then undefined). */
+int psvd_update_adjoint(psvd_handle h, int32_t kc, const float* U, int64_t ldu, const double* D,
+                        const void* A, int64_t lda, int32_t B, int32_t dtype, int32_t k1,
+                        const float* U_new, int64_t ld_new, const double* D_new,
+                        const float* U_new_bar, int64_t ld_new_bar, const double* D_new_bar,
+                        float* U_bar, int64_t ld_bar, double* D_bar, float* A_bar,
+                        int64_t lda_bar);
 
 /* psvd_set_profiling: enable (1) or disable (0) per-phase CUDA-event timing on
  * the handle's stream and reset its counters.  Phases: 0 panel Gram (partials

@@ -48,6 +48,7 @@ struct psvd_ctx {
   size_t staging_bytes = 0;
   float* Uf32_tmp = nullptr;  // FP32 view of hi/lo modes for get_modes / save
   ApmosCache* apmos = nullptr;  // psvd_parallel_svd workspaces and streams (lazily made)
+  AdjWork* adj = nullptr;       // psvd_update_adjoint workspaces (lazily made)
   int host_info[4] = {0, 0, 0, 0};
   int sticky_status = 0;
   // per-phase event timing (psvd_set_profiling)
@@ -300,6 +301,8 @@ const char* psvd_status_string(int s) {
     case PSVD_OK: return "ok";
     case PSVD_WARN_RANK_DEFICIENT: return "warning: a kept singular value is numerically zero";
     case PSVD_WARN_NOT_CONVERGED: return "warning: Jacobi eigen-solve reached its sweep limit";
+    case PSVD_WARN_DEGENERATE:
+      return "warning: coincident singular values at a kept index; the derivative is undefined";
     case PSVD_ERR_INVALID_ARG: return "invalid argument";
     case PSVD_ERR_NOT_INITIALIZED: return "handle not initialized (call psvd_initialize first)";
     case PSVD_ERR_SHAPE: return "unsupported shape";
@@ -457,6 +460,7 @@ void psvd_destroy(psvd_handle h) {
   cudaFree(h->staging);
   cudaFree(h->Uf32_tmp);
   apmos_cache_destroy(h->apmos);
+  adj_work_destroy(h->adj);
   cudaFree(h->w.T64);
   cudaGetLastError();
   delete h;
@@ -593,6 +597,36 @@ int psvd_parallel_svd(psvd_handle h, const void* A, int64_t lda, const int64_t* 
   if (rc != PSVD_OK) return rc;
   if (bits & 4) return PSVD_ERR_NONFINITE;
   return (bits & 1) ? PSVD_WARN_RANK_DEFICIENT : PSVD_OK;
+}
+
+int psvd_update_adjoint(psvd_handle h, int32_t kc, const float* U, int64_t ldu, const double* D,
+                        const void* A, int64_t lda, int32_t B, int32_t dtype, int32_t k1,
+                        const float* U_new, int64_t ld_new, const double* D_new,
+                        const float* U_new_bar, int64_t ld_new_bar, const double* D_new_bar,
+                        float* U_bar, int64_t ld_bar, double* D_bar, float* A_bar,
+                        int64_t lda_bar) {
+  if (!h || kc < 0 || B < 1 || k1 < 1) return PSVD_ERR_INVALID_ARG;
+  if (dtype != PSVD_F32 && dtype != PSVD_BF16) return PSVD_ERR_INVALID_ARG;
+  const int64_t M = h->M;
+  const int n = kc + B;
+  if (n > kMaxN || k1 > n || k1 > 64 || M < n) return PSVD_ERR_SHAPE;
+  if (!A || !U_new || !D_new || !U_new_bar || !D_new_bar || !A_bar) return PSVD_ERR_INVALID_ARG;
+  if (kc > 0 && (!U || !D || !U_bar || !D_bar)) return PSVD_ERR_INVALID_ARG;
+  if (lda < M || ld_new < M || ld_new_bar < M || lda_bar < M || (kc > 0 && (ldu < M || ld_bar < M)))
+    return PSVD_ERR_INVALID_ARG;
+  // the M-row operands are read and written in place on the device
+  if (!is_device_ptr(A) || !is_device_ptr(U_new) || !is_device_ptr(U_new_bar) ||
+      !is_device_ptr(A_bar) || (kc > 0 && (!is_device_ptr(U) || !is_device_ptr(U_bar))))
+    return PSVD_ERR_INVALID_ARG;
+  if (!h->adj) h->adj = adj_work_create();
+  if (!h->adj) return PSVD_ERR_ALLOC;
+  int bits = 0;
+  const int rc = adjoint_run(h->adj, h->st, h->num_sms, M, h->cfg.ff, kc, U, ldu, D, A, lda,
+                             dtype == PSVD_BF16 ? 1 : 0, B, k1, U_new, ld_new, D_new, U_new_bar,
+                             ld_new_bar, D_new_bar, U_bar, ld_bar, D_bar, A_bar, lda_bar, &bits);
+  if (rc != PSVD_OK) return rc;
+  if (bits & 4) return PSVD_ERR_NONFINITE;
+  return (bits & 3) ? PSVD_WARN_DEGENERATE : PSVD_OK;
 }
 
 int psvd_set_profiling(psvd_handle h, int32_t enable) {

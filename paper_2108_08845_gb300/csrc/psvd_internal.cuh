@@ -162,14 +162,32 @@ cudaError_t randomized_solve_launch(const RandWork& r, const SmallWork& w, int n
 // Algorithm 2 on device data: A (Mtot x N, lda, FP32 or BF16) in row blocks
 // [off[b], off[b+1]) (host array), r1 local and r2 global modes; U (Mtot x r2,
 // FP32, ldu) and L (r2, FP64) on the device.  *status receives the accumulated
-// status bits (1 rank deficient, 4 non-finite).  Allocates and frees its own
-// workspace; synchronises the stream.
+// status bits (1 rank deficient, 4 non-finite).  Workspaces, lane streams and the
+// captured launch graph live in the cache; synchronises the stream.
 struct ApmosCache;
 ApmosCache* apmos_cache_create();
 void apmos_cache_destroy(ApmosCache* c);
 int apmos_run(const void* A, int64_t lda, int a_bf16, int64_t Mtot, const int64_t* off, int nparts,
               int N, int r1, int r2, float* U, int64_t ldu, double* L, int num_sms,
               cudaStream_t st, ApmosCache* cache, int* status);
+
+// ------------------------------------------------------------------ adjoint
+// Reverse-mode derivative of one update of Algorithm 1 (adjoint.cu).  Inputs: the
+// step's panel pieces U (M x kc FP32; kc = 0 at the initialisation), D (kc), A
+// (M x B, FP32 or BF16), its outputs U' (M x k1 FP32) and D' (k1), and their
+// cotangents Ybar (M x k1 FP32) and sbar (k1).  Outputs Ubar (M x kc), Dbar (kc),
+// Abar (M x B, FP32).  M-sized arrays are device pointers; D, D', sbar and Dbar may
+// be host or device.  Workspaces live in the AdjWork; synchronises the stream.
+// *status receives bits: 1 two kept singular values coincide, 2 a kept singular
+// value meets a dropped one, 4 a non-finite coefficient.
+struct AdjWork;
+AdjWork* adj_work_create();
+void adj_work_destroy(AdjWork* w);
+int adjoint_run(AdjWork* aw, cudaStream_t st, int num_sms, int64_t M, double ff, int kc,
+                const float* U, int64_t ldu, const double* D, const void* A, int64_t lda,
+                int a_bf16, int B, int k1, const float* Unew, int64_t ldun, const double* Dnew,
+                const float* Ybar, int64_t ldyb, const double* sbar, float* Ubar, int64_t ldub,
+                double* Dbar, float* Abar, int64_t ldab, int* status);
 
 // -------------------------------------------------------------------- Philox
 cudaError_t gaussian_sketch_launch(uint64_t seed, uint64_t stream_id, int64_t rows, int64_t cols,

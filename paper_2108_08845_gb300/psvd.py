@@ -22,6 +22,7 @@ from . import build as _build
 PSVD_OK = 0
 PSVD_WARN_RANK_DEFICIENT = 1
 PSVD_WARN_NOT_CONVERGED = 2
+PSVD_WARN_DEGENERATE = 3
 PSVD_ERR_INVALID_ARG = -1
 PSVD_ERR_NOT_INITIALIZED = -2
 PSVD_ERR_SHAPE = -3
@@ -92,6 +93,8 @@ def load(build_if_missing: bool = True):
         lib.psvd_status_string.restype = C.c_char_p
         lib.psvd_last_info.argtypes = [vp, C.POINTER(C.c_int32)]
         lib.psvd_parallel_qr_static.argtypes = [vp, i64, i64, i32, i32, vp, vp]
+        lib.psvd_update_adjoint.argtypes = [vp, i32, vp, i64, vp, vp, i64, i32, i32, i32, vp, i64,
+                                            vp, vp, i64, vp, vp, i64, vp, vp, i64]
         lib.psvd_set_profiling.argtypes = [vp, i32]
         lib.psvd_get_profile.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                          C.POINTER(C.c_int64)]
@@ -255,6 +258,38 @@ def psvd_gaussian_sketch(seed: int, stream_id: int, out, stream=None) -> int:
         raise ValueError("out must be a contiguous column-major float32 matrix")
     return _check(load().psvd_gaussian_sketch(int(seed), int(stream_id), rows, cols, p,
                                               _stream_ptr(stream)), "psvd_gaussian_sketch")
+
+
+def psvd_update_adjoint(h: int, U, D, A, U_new, D_new, U_new_bar, D_new_bar, U_bar, D_bar,
+                        A_bar) -> int:
+    """Cotangents (U_bar, D_bar, A_bar) of one step's inputs from those of its outputs
+    (include/psvd.h).  U, D, U_bar, D_bar are None for the initialisation step.
+    Returns PSVD_OK or PSVD_WARN_DEGENERATE."""
+    a, lda, M, B, acode, _k1 = _mat(A, "A")
+    un, ldn, _, k1, ucode, _k2 = _mat(U_new, "U_new")
+    ub, ldb, _, _, bcode, _k3 = _mat(U_new_bar, "U_new_bar")
+    ab, ldab, _, _, abcode, _k4 = _mat(A_bar, "A_bar")
+    dn, _, _, _, dcode, _k5 = _mat(D_new, "D_new", allow_f64=True)
+    db, _, _, _, dbcode, _k6 = _mat(D_new_bar, "D_new_bar", allow_f64=True)
+    if ucode != PSVD_F32 or bcode != PSVD_F32 or abcode != PSVD_F32:
+        raise ValueError("U_new, U_new_bar and A_bar must be float32")
+    if dcode != PSVD_F64 or dbcode != PSVD_F64:
+        raise ValueError("D_new and D_new_bar must be float64")
+    if U is None:
+        kc, u, ldu, d, ubar, ldub, dbar = 0, None, M, None, None, M, None
+        keep = ()
+    else:
+        u, ldu, _, kc, c1, k7 = _mat(U, "U")
+        d, _, _, _, c2, k8 = _mat(D, "D", allow_f64=True)
+        ubar, ldub, _, _, c3, k9 = _mat(U_bar, "U_bar")
+        dbar, _, _, _, c4, k10 = _mat(D_bar, "D_bar", allow_f64=True)
+        if c1 != PSVD_F32 or c3 != PSVD_F32 or c2 != PSVD_F64 or c4 != PSVD_F64:
+            raise ValueError("U, U_bar must be float32 and D, D_bar float64")
+        keep = (k7, k8, k9, k10)
+    rc = load().psvd_update_adjoint(h, kc, u, ldu, d, a, lda, B, acode, k1, un, ldn, dn, ub, ldb,
+                                    db, ubar, ldub, dbar, ab, ldab)
+    del keep
+    return _check(rc, "psvd_update_adjoint")
 
 
 def psvd_last_info(h: int):
