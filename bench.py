@@ -282,8 +282,9 @@ def reference_main(args):
 def apmos_main(args):
     """Algorithm 2 (APMOS) on the batching workload: 64 row partitions of uniform
     sizes in [16,384, 262,144] rows (seeded), 64 snapshots, r1 = 20 local modes,
-    r2 = 20 global modes, FP32; one psvd_parallel_svd call per step (workspace
-    allocation included).  A secondary measurement, printed as its own JSON line."""
+    r2 = 20 global modes, FP32; one psvd_parallel_svd call per step (the handle keeps
+    its workspaces and launch graph after the first call).  A secondary measurement,
+    printed as its own JSON line."""
     import numpy as np
     import torch
 
@@ -322,6 +323,74 @@ def apmos_main(args):
     return 0
 
 
+def streams_main(args):
+    """Many independent snapshot streams (the batching workload's second part): 32
+    streams of M = 65,536 rows, K = 16 modes, B = 16 snapshots per update, FP32, all
+    updated by one psvd_group_incorporate_data call per step (fork/join over 32 CUDA
+    streams, captured into a graph and replayed).  Each stream's batches alternate
+    between two resident device buffers.  Also timed: the same 32 updates through 32
+    lone handles one after another on one stream.  Printed as its own JSON line."""
+    import torch
+
+    from paper_2108_08845_gb300 import psvd, synthetic
+    torch.cuda.set_device(0)
+    count, M, K, B, ff = 32, 65536, 16, 16, 0.95
+    g = torch.Generator(device="cuda").manual_seed(SEED + 3)
+    bufs = []
+    for i in range(count):
+        pair = []
+        for _ in range(2):
+            A = torch.randn(M, 24, device="cuda", generator=g) @ torch.randn(24, B, device="cuda",
+                                                                             generator=g)
+            pair.append((A + 1e-3 * torch.randn(M, B, device="cuda", generator=g)).T.contiguous().T)
+        bufs.append(pair)
+    stream = torch.cuda.current_stream()
+
+    def timed(step_fn, steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for t in range(steps):
+            step_fn(t)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    grp = psvd.psvd_group_create(count, M, K, B, ff, psvd.PSVD_PREC_FP32)
+    psvd.psvd_group_initialize(grp, [b[0] for b in bufs])
+    gstep = lambda t: psvd.psvd_group_incorporate_data(grp, [b[(t + 1) % 2] for b in bufs])
+    for t in range(args.warmup):
+        gstep(t)
+    ms = timed(lambda t: gstep(t + args.warmup), args.steps)
+    captures, replays = psvd.psvd_group_stats(grp)
+    rc = psvd.psvd_group_status(grp)
+    psvd.psvd_group_destroy(grp)
+    hs = [psvd.StreamingSVD(M, K, B, ff, psvd.PSVD_PREC_FP32) for _ in range(count)]
+    for i, h in enumerate(hs):
+        h.initialize(bufs[i][0])
+
+    def lone(t):
+        for i, h in enumerate(hs):
+            psvd.psvd_incorporate_data(h.h, bufs[i][(t + 1) % 2])
+
+    for t in range(args.warmup):
+        lone(t)
+    ms_lone = timed(lambda t: lone(t + args.warmup), args.steps)
+    for h in hs:
+        h.close()
+    byt = count * M * (2 * 4 * (K + B) + 4 * K)  # Gram and update read U and A, update writes U
+    print(json.dumps({"metric": "snapshots/s over 32 independent streams (M=65,536, K=16, B=16, FP32)",
+                      "value": count * B / (ms * 1e-3), "unit": "snapshots/s", "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                      "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": "streams", "streams": count, "M": M, "K": K, "B": B,
+                                 "ff": ff, "inputs": "two resident device buffers per stream"},
+                      "graph": {"captures": captures, "replays": replays}, "status": rc,
+                      "lone_handles_ms_per_step": ms_lone,
+                      "algorithmic_bytes": byt, "achieved_gbs": byt / (ms * 1e-3) / 1e9}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -333,8 +402,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--ny", type=int, default=NY, help="grid rows (profiling on smaller grids)")
     ap.add_argument("--nx", type=int, default=NX, help="grid columns")
-    ap.add_argument("--workload", default="stream", choices=["stream", "apmos"],
-                    help="stream: the streaming update (headline); apmos: Algorithm 2 batching")
+    ap.add_argument("--workload", default="stream", choices=["stream", "apmos", "streams"],
+                    help="stream: the streaming update (headline); apmos: Algorithm 2 batching; "
+                         "streams: 32 independent streams per captured graph")
     args = ap.parse_args()
     set_grid(args.ny, args.nx)
     if args.warmup < 3:
@@ -343,6 +413,8 @@ def main():
         return reference_main(args)
     if args.workload == "apmos":
         return apmos_main(args)
+    if args.workload == "streams":
+        return streams_main(args)
 
     import torch
 

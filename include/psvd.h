@@ -244,6 +244,38 @@ int psvd_update_adjoint(psvd_handle h, int32_t kc, const float* U, int64_t ldu, 
                         float* U_bar, int64_t ld_bar, double* D_bar, float* A_bar,
                         int64_t lda_bar);
 
+/* ------------------------------------------------------------------ groups
+ * Many independent snapshot streams updated together (the batching form of the
+ * method: one Algorithm 1 state per stream).  psvd_group_create makes `count`
+ * handles with the same configuration, each on a CUDA stream of its own; cfg->stream
+ * is the stream the group's calls are ordered on (their work starts after the
+ * caller's earlier work on it, and later work on it waits for theirs).
+ *
+ * psvd_group_initialize / psvd_group_incorporate_data apply psvd_initialize /
+ * psvd_incorporate_data to every member i with its own batch A[i] (A: host array
+ * of `count` pointers; each batch M x B, leading dimension lda, dtype as for the
+ * single-handle calls).  The members' update sequences run concurrently.  Once
+ * every member holds K modes (and the handles use neither the randomized front
+ * end nor the tensor-core path), the fork / updates / join sequence is captured
+ * into a CUDA graph, one per double-buffer parity, and replayed by later calls
+ * whose batch pointers, lda, B and dtype repeat (a ring of input buffers reuses
+ * the graphs; new pointers are captured anew).  The calls do not synchronise;
+ * psvd_group_status reads every member's status (synchronising) and returns the
+ * most severe.  Members are ordinary handles for psvd_get_modes,
+ * psvd_get_singular_values, psvd_save, ... (psvd_group_member); do not update a
+ * member outside the group or destroy it.  psvd_group_stats reports how many
+ * calls captured a graph and how many replayed one. */
+typedef struct psvd_group* psvd_group_handle;
+int psvd_group_create(psvd_group_handle* out, int32_t count, const psvd_config* cfg);
+void psvd_group_destroy(psvd_group_handle g);
+int psvd_group_initialize(psvd_group_handle g, const void* const* A, int64_t lda, int32_t B,
+                          int32_t dtype);
+int psvd_group_incorporate_data(psvd_group_handle g, const void* const* A, int64_t lda,
+                                int32_t B, int32_t dtype);
+psvd_handle psvd_group_member(psvd_group_handle g, int32_t i);
+int psvd_group_status(psvd_group_handle g);
+int psvd_group_stats(psvd_group_handle g, int64_t* captures, int64_t* replays);
+
 /* psvd_set_profiling: enable (1) or disable (0) per-phase CUDA-event timing on
  * the handle's stream and reset its counters.  Phases: 0 panel Gram (partials
  * and reduction), 1 small solve (eigen-decomposition, refinement, T), 2 mode

@@ -629,6 +629,236 @@ int psvd_update_adjoint(psvd_handle h, int32_t kc, const float* U, int64_t ldu, 
   return (bits & 3) ? PSVD_WARN_DEGENERATE : PSVD_OK;
 }
 
+// ------------------------------------------------------------------ groups
+// Many independent snapshot streams (one handle each, on its own stream) updated
+// together: one call forks the members' update sequences onto their streams and
+// joins them.  In steady state (every member at K modes, no randomized front end,
+// not the tensor-core path) the whole fork/updates/join sequence is captured into
+// a CUDA graph, one per double-buffer parity, and replayed while the arguments
+// (batch pointers, lda, B, dtype, member states) repeat.
+struct psvd_group {
+  std::vector<psvd_handle> m;
+  std::vector<cudaStream_t> ms;   // member streams (owned)
+  std::vector<cudaEvent_t> done;  // per-member join events
+  cudaStream_t user = nullptr;    // the configuration's stream
+  cudaStream_t origin = nullptr;  // capture origin (owned, non-blocking)
+  cudaEvent_t in = nullptr, out = nullptr, fork = nullptr;
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int64_t> key;
+    std::vector<int64_t> launches;  // per member
+  } graph[2];
+  int64_t replays = 0, captures = 0;
+};
+
+namespace {
+
+void group_free(psvd_group* g) {
+  if (!g) return;
+  if (g->origin) cudaStreamSynchronize(g->origin);
+  for (auto& gr : g->graph)
+    if (gr.exec) cudaGraphExecDestroy(gr.exec);
+  for (psvd_handle h : g->m) psvd_destroy(h);
+  for (cudaStream_t st : g->ms) cudaStreamDestroy(st);
+  for (cudaEvent_t e : g->done) cudaEventDestroy(e);
+  if (g->origin) cudaStreamDestroy(g->origin);
+  if (g->in) cudaEventDestroy(g->in);
+  if (g->out) cudaEventDestroy(g->out);
+  if (g->fork) cudaEventDestroy(g->fork);
+  cudaGetLastError();
+  delete g;
+}
+
+// Forks the members' steps off the origin stream and joins them back.
+int group_enqueue(psvd_group* g, const void* const* A, int64_t lda, int B, int dtype, bool init) {
+  CK(cudaEventRecord(g->fork, g->origin));
+  for (size_t i = 0; i < g->m.size(); ++i) {
+    psvd_handle h = g->m[i];
+    CK(cudaStreamWaitEvent(h->st, g->fork, 0));
+    const int rc = init ? psvd_initialize(h, A[i], lda, B, dtype)
+                        : psvd_incorporate_data(h, A[i], lda, B, dtype);
+    if (rc < 0) return rc;
+    CK(cudaEventRecord(g->done[i], h->st));
+    CK(cudaStreamWaitEvent(g->origin, g->done[i], 0));
+  }
+  return PSVD_OK;
+}
+
+int group_step(psvd_group* g, const void* const* A, int64_t lda, int32_t B, int32_t dtype,
+               bool init) {
+  if (!g || !A) return PSVD_ERR_INVALID_ARG;
+  const size_t n = g->m.size();
+  bool steady = !init;
+  for (size_t i = 0; i < n; ++i) {
+    psvd_handle h = g->m[i];
+    if (!init && h->kc == 0) return PSVD_ERR_NOT_INITIALIZED;
+    if (int rc = check_batch(h, A[i], lda, B, dtype)) return rc;
+    steady = steady && h->kc == h->K && !h->cfg.low_rank && !use_tc(h) && !h->profiling &&
+             is_device_ptr(A[i]);
+  }
+  CK(cudaEventRecord(g->in, g->user));
+  CK(cudaStreamWaitEvent(g->origin, g->in, 0));
+  std::vector<int64_t> key;
+  if (steady) {
+    key = {lda, B, dtype};
+    for (size_t i = 0; i < n; ++i) {
+      key.push_back((int64_t)(uintptr_t)A[i]);
+      key.push_back(g->m[i]->cur);
+    }
+  }
+  const int parity = n ? g->m[0]->cur : 0;
+  psvd_group::Graph& gr = g->graph[parity];
+  bool graph_ran = false;
+  if (steady && gr.exec && gr.key == key) {
+    graph_ran = true;
+    CK(cudaGraphLaunch(gr.exec, g->origin));
+    // the host-side state the captured steps advanced (kc stays K)
+    for (size_t i = 0; i < n; ++i) {
+      psvd_handle h = g->m[i];
+      h->cur ^= 1;
+      h->iteration += 1;
+      h->launches += gr.launches[i];
+    }
+    ++g->replays;
+  } else {
+    bool captured = false;
+    if (steady) {
+      // grow the members' Gram partials outside the capture (growing synchronises)
+      for (size_t i = 0; i < n; ++i) {
+        psvd_handle h = g->m[i];
+        int nchunk;
+        int64_t rpc, pd;
+        gram_simt_plan(h->M, h->kc + B, h->num_sms, &nchunk, &rpc, &pd);
+        if (int rc = ensure_partial(h, pd)) return rc;
+      }
+      struct Saved {
+        int cur, kc;
+        int64_t iteration, launches;
+      };
+      std::vector<Saved> saved(n);
+      for (size_t i = 0; i < n; ++i)
+        saved[i] = {g->m[i]->cur, g->m[i]->kc, g->m[i]->iteration, g->m[i]->launches};
+      cudaGraph_t graph = nullptr;
+      if (cudaStreamBeginCapture(g->origin, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+        const int rc = group_enqueue(g, A, lda, B, dtype, false);
+        const cudaError_t ec = cudaStreamEndCapture(g->origin, &graph);
+        cudaGraphExec_t exec = nullptr;
+        if (rc == PSVD_OK && ec == cudaSuccess && graph &&
+            cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+          if (gr.exec) cudaGraphExecDestroy(gr.exec);
+          gr.exec = exec;
+          gr.key = key;
+          gr.launches.assign(n, 0);
+          for (size_t i = 0; i < n; ++i) gr.launches[i] = g->m[i]->launches - saved[i].launches;
+          captured = true;
+        }
+        if (graph) cudaGraphDestroy(graph);
+      }
+      cudaGetLastError();
+      if (captured) {
+        CK(cudaGraphLaunch(gr.exec, g->origin));
+        graph_ran = true;
+        ++g->captures;
+      } else {
+        // nothing was enqueued: undo the host-side steps and run them directly
+        for (size_t i = 0; i < n; ++i) {
+          psvd_handle h = g->m[i];
+          h->cur = saved[i].cur;
+          h->kc = saved[i].kc;
+          h->iteration = saved[i].iteration;
+          h->launches = saved[i].launches;
+        }
+      }
+    }
+    if (!captured)
+      if (int rc = group_enqueue(g, A, lda, B, dtype, init)) return rc;
+  }
+  CK(cudaEventRecord(g->out, g->origin));
+  CK(cudaStreamWaitEvent(g->user, g->out, 0));
+  // a graph runs the members' work on the origin stream: later work on a member's
+  // own stream (psvd_get_modes, a direct step) must wait for it
+  if (graph_ran)
+    for (size_t i = 0; i < n; ++i) CK(cudaStreamWaitEvent(g->m[i]->st, g->out, 0));
+  return PSVD_OK;
+}
+
+}  // namespace
+
+int psvd_group_create(psvd_group_handle* out, int32_t count, const psvd_config* cfg) {
+  if (!out) return PSVD_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!cfg || count < 1) return PSVD_ERR_INVALID_ARG;
+  psvd_group* g = new (std::nothrow) psvd_group();
+  if (!g) return PSVD_ERR_ALLOC;
+  g->user = (cudaStream_t)cfg->stream;
+  bool ok = cudaStreamCreateWithFlags(&g->origin, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&g->in, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&g->out, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming) == cudaSuccess;
+  int rc = ok ? PSVD_OK : PSVD_ERR_CUDA;
+  for (int i = 0; rc == PSVD_OK && i < count; ++i) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t e = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      rc = PSVD_ERR_CUDA;
+      break;
+    }
+    g->ms.push_back(st);
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      rc = PSVD_ERR_CUDA;
+      break;
+    }
+    g->done.push_back(e);
+    psvd_config c = *cfg;
+    c.stream = st;
+    psvd_handle h = nullptr;
+    rc = psvd_create(&h, &c);
+    if (rc == PSVD_OK) g->m.push_back(h);
+  }
+  if (rc != PSVD_OK) {
+    cudaGetLastError();
+    group_free(g);
+    return rc;
+  }
+  *out = g;
+  return PSVD_OK;
+}
+
+void psvd_group_destroy(psvd_group_handle g) { group_free(g); }
+
+int psvd_group_initialize(psvd_group_handle g, const void* const* A, int64_t lda, int32_t B,
+                          int32_t dtype) {
+  return group_step(g, A, lda, B, dtype, true);
+}
+
+int psvd_group_incorporate_data(psvd_group_handle g, const void* const* A, int64_t lda,
+                                int32_t B, int32_t dtype) {
+  return group_step(g, A, lda, B, dtype, false);
+}
+
+psvd_handle psvd_group_member(psvd_group_handle g, int32_t i) {
+  if (!g || i < 0 || (size_t)i >= g->m.size()) return nullptr;
+  return g->m[i];
+}
+
+int psvd_group_stats(psvd_group_handle g, int64_t* captures, int64_t* replays) {
+  if (!g) return PSVD_ERR_INVALID_ARG;
+  if (captures) *captures = g->captures;
+  if (replays) *replays = g->replays;
+  return PSVD_OK;
+}
+
+int psvd_group_status(psvd_group_handle g) {
+  if (!g) return PSVD_ERR_INVALID_ARG;
+  int worst = PSVD_OK;
+  for (psvd_handle h : g->m) {
+    const int rc = collect_status(h);
+    if (rc < 0 && (worst >= 0 || rc < worst)) worst = rc;
+    if (worst >= 0 && rc > worst) worst = rc;
+  }
+  return worst;
+}
+
 int psvd_set_profiling(psvd_handle h, int32_t enable) {
   if (!h) return PSVD_ERR_INVALID_ARG;
   prof_collect(h);

@@ -95,6 +95,15 @@ def load(build_if_missing: bool = True):
         lib.psvd_parallel_qr_static.argtypes = [vp, i64, i64, i32, i32, vp, vp]
         lib.psvd_update_adjoint.argtypes = [vp, i32, vp, i64, vp, vp, i64, i32, i32, i32, vp, i64,
                                             vp, vp, i64, vp, vp, i64, vp, vp, i64]
+        lib.psvd_group_create.argtypes = [C.POINTER(vp), i32, C.POINTER(psvd_config)]
+        lib.psvd_group_destroy.argtypes = [vp]
+        lib.psvd_group_destroy.restype = None
+        lib.psvd_group_initialize.argtypes = [vp, C.POINTER(vp), i64, i32, i32]
+        lib.psvd_group_incorporate_data.argtypes = [vp, C.POINTER(vp), i64, i32, i32]
+        lib.psvd_group_member.argtypes = [vp, i32]
+        lib.psvd_group_member.restype = vp
+        lib.psvd_group_status.argtypes = [vp]
+        lib.psvd_group_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         lib.psvd_set_profiling.argtypes = [vp, i32]
         lib.psvd_get_profile.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                          C.POINTER(C.c_int64)]
@@ -309,6 +318,62 @@ def psvd_get_profile(h: int):
     nl = C.c_int64()
     _check(load().psvd_get_profile(h, ms, cnt, C.byref(nl)), "psvd_get_profile")
     return [float(x) for x in ms], [int(x) for x in cnt], int(nl.value)
+
+
+def _batch_list(batches, where: str):
+    mats = [_mat(b, f"{where}[{i}]", allow_f64=True) for i, b in enumerate(batches)]
+    if not mats:
+        raise ValueError(f"{where}: no batches")
+    ld, B, code = mats[0][1], mats[0][3], mats[0][4]
+    for m in mats:
+        if (m[1], m[3], m[4]) != (ld, B, code):
+            raise ValueError(f"{where}: every batch needs the same lda, B and dtype")
+    ptrs = (C.c_void_p * len(mats))(*[m[0] for m in mats])
+    return ptrs, ld, B, code, mats
+
+
+def psvd_group_create(count: int, M: int, K: int, max_batch: int, ff: float = 1.0,
+                      precision: int = PSVD_PREC_FP32, low_rank: int = 0, oversample: int = 10,
+                      power_iters: int = 0, seed: int = 0, stream=None) -> int:
+    lib = load()
+    cfg = psvd_config(int(M), int(K), int(max_batch), float(ff), int(precision), int(low_rank),
+                      int(oversample), int(power_iters), int(seed), _stream_ptr(stream))
+    g = C.c_void_p()
+    _check(lib.psvd_group_create(C.byref(g), int(count), C.byref(cfg)), "psvd_group_create")
+    return g.value
+
+
+def psvd_group_destroy(g: int) -> None:
+    load().psvd_group_destroy(g)
+
+
+def psvd_group_initialize(g: int, batches) -> int:
+    ptrs, ld, B, code, _keep = _batch_list(batches, "batches")
+    return _check(load().psvd_group_initialize(g, ptrs, ld, B, code), "psvd_group_initialize")
+
+
+def psvd_group_incorporate_data(g: int, batches) -> int:
+    ptrs, ld, B, code, _keep = _batch_list(batches, "batches")
+    return _check(load().psvd_group_incorporate_data(g, ptrs, ld, B, code),
+                  "psvd_group_incorporate_data")
+
+
+def psvd_group_member(g: int, i: int) -> int:
+    h = load().psvd_group_member(g, int(i))
+    if not h:
+        raise PsvdError(PSVD_ERR_INVALID_ARG, "psvd_group_member")
+    return h
+
+
+def psvd_group_status(g: int) -> int:
+    return _check(load().psvd_group_status(g), "psvd_group_status")
+
+
+def psvd_group_stats(g: int):
+    """(captures, replays): calls that captured a CUDA graph, calls that replayed one."""
+    c, r = C.c_int64(), C.c_int64()
+    _check(load().psvd_group_stats(g, C.byref(c), C.byref(r)), "psvd_group_stats")
+    return int(c.value), int(r.value)
 
 
 class StreamingSVD:
