@@ -328,8 +328,9 @@ def streams_main(args):
     streams of M = 65,536 rows, K = 16 modes, B = 16 snapshots per update, FP32, all
     updated by one psvd_group_incorporate_data call per step (fork/join over 32 CUDA
     streams, captured into a graph and replayed).  Each stream's batches alternate
-    between two resident device buffers.  Also timed: the same 32 updates through 32
-    lone handles one after another on one stream.  Printed as its own JSON line."""
+    between two resident device buffers; tile shapes come from psvd_autotune.  Also
+    timed: the same 32 updates through 32 lone handles (same tiles) one after another
+    on one stream.  Printed as its own JSON line."""
     import torch
 
     from paper_2108_08845_gb300 import psvd, synthetic
@@ -358,6 +359,8 @@ def streams_main(args):
 
     grp = psvd.psvd_group_create(count, M, K, B, ff, psvd.PSVD_PREC_FP32)
     psvd.psvd_group_initialize(grp, [b[0] for b in bufs])
+    # tile shapes for this panel shape: timed once, then taken from the per-shape cache
+    tune = [psvd.psvd_autotune(psvd.psvd_group_member(grp, i), bufs[i][1]) for i in range(count)][0]
     gstep = lambda t: psvd.psvd_group_incorporate_data(grp, [b[(t + 1) % 2] for b in bufs])
     for t in range(args.warmup):
         gstep(t)
@@ -368,6 +371,7 @@ def streams_main(args):
     hs = [psvd.StreamingSVD(M, K, B, ff, psvd.PSVD_PREC_FP32) for _ in range(count)]
     for i, h in enumerate(hs):
         h.initialize(bufs[i][0])
+        psvd.psvd_autotune(h.h, bufs[i][1])
 
     def lone(t):
         for i, h in enumerate(hs):
@@ -386,6 +390,7 @@ def streams_main(args):
                       "config": {"workload": "streams", "streams": count, "M": M, "K": K, "B": B,
                                  "ff": ff, "inputs": "two resident device buffers per stream"},
                       "graph": {"captures": captures, "replays": replays}, "status": rc,
+                      "tiles": {"gram_ctas_per_sm": tune[0], "update_rows": tune[1]},
                       "lone_handles_ms_per_step": ms_lone,
                       "algorithmic_bytes": byt, "achieved_gbs": byt / (ms * 1e-3) / 1e9}))
     return 0

@@ -244,6 +244,21 @@ int psvd_update_adjoint(psvd_handle h, int32_t kc, const float* U, int64_t ldu, 
                         float* U_bar, int64_t ld_bar, double* D_bar, float* A_bar,
                         int64_t lda_bar);
 
+/* psvd_autotune: picks the FP32 path's tile shapes for this handle's steady-state
+ * panel (M rows, n = K + B columns) by timing the candidates on the handle's stream
+ * with a representative batch A (DEVICE pointer, M x B, lda >= M, PSVD_F32 or
+ * PSVD_BF16): Gram row chunks sized for 1, 2, 4 or 8 resident CTAs per SM, and
+ * mode-update tiles of 64 or 128 rows.  The fastest of each is kept by the handle
+ * and cached for the process under (M, n, dtype, SM count), so later calls with the
+ * same shape take it without timing.  The choice changes only the summation order
+ * of the Gram's row chunks (results stay within the same rounding bounds).
+ * choice (may be null) receives {CTAs per SM, update tile rows}.  FP32 handles only
+ * (PSVD_ERR_UNSUPPORTED otherwise).  Synchronises; the handle's modes, singular
+ * values and status are unchanged.  Call it between updates, not inside a group's
+ * steady state (a changed tile re-captures the group's graphs). */
+int psvd_autotune(psvd_handle h, const void* A, int64_t lda, int32_t B, int32_t dtype,
+                  int32_t* choice);
+
 /* ------------------------------------------------------------------ groups
  * Many independent snapshot streams updated together (the batching form of the
  * method: one Algorithm 1 state per stream).  psvd_group_create makes `count`

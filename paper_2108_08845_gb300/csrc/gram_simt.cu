@@ -149,20 +149,22 @@ __global__ void gram_reduce_kernel(const double* __restrict__ partial, int nchun
   if (!isfinite(s)) atomicOr(&info[2], 4);
 }
 
-constexpr int UR = 128;  // rows per update tile
 constexpr int UC = 64;   // output columns per update tile
 constexpr int UK = 32;   // panel columns per stage
 
+// Tile of UR = 32 RI rows x UC columns; each thread holds RI rows x 8 columns.
+template <int RI>
 __global__ void __launch_bounds__(256) update_kernel(PanelF32 p, const float* __restrict__ T, int k1,
                                                      float* __restrict__ Unew, int64_t ldo) {
+  constexpr int UR = 32 * RI;
   __shared__ __align__(16) float Ps[UK * UR];
   __shared__ __align__(16) float Ts[UK * UC];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t r0 = (int64_t)blockIdx.x * UR;
   const int j0 = blockIdx.y * UC;
-  float acc[4][8];
+  float acc[RI][8];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < RI; ++i)
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
 
@@ -180,20 +182,20 @@ __global__ void __launch_bounds__(256) update_kernel(PanelF32 p, const float* __
     __syncthreads();
 #pragma unroll 4
     for (int c = 0; c < UK; ++c) {
-      float pv[4];
+      float pv[RI];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) pv[i] = Ps[c * UR + lane + 32 * i];
+      for (int i = 0; i < RI; ++i) pv[i] = Ps[c * UR + lane + 32 * i];
       const float4 t0 = *reinterpret_cast<const float4*>(&Ts[c * UC + 8 * warp]);
       const float4 t1 = *reinterpret_cast<const float4*>(&Ts[c * UC + 8 * warp + 4]);
       const float tv[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < RI; ++i)
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(pv[i], tv[j], acc[i][j]);
     }
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < RI; ++i) {
     const int64_t row = r0 + lane + 32 * i;
     if (row >= p.M) continue;
 #pragma unroll
@@ -215,11 +217,11 @@ __global__ void copy_modes_kernel(const float* __restrict__ U, int64_t ldu, int6
 }  // namespace
 
 void gram_simt_plan(int64_t M, int n, int num_sms, int* nchunk, int64_t* rows_per_chunk,
-                    int64_t* partial_doubles) {
+                    int64_t* partial_doubles, int ctas_per_sm) {
   const int nb = (int)ceil_div(n, GB);
   const int npairs = nb * (nb + 1) / 2;
-  // about 4 resident CTAs per SM in total, chunks a multiple of the stage height
-  int64_t want = (int64_t)num_sms * 4 / npairs;
+  // about ctas_per_sm CTAs per SM in total, chunks a multiple of the stage height
+  int64_t want = (int64_t)num_sms * (ctas_per_sm > 0 ? ctas_per_sm : 4) / npairs;
   if (want < 1) want = 1;
   int64_t rpc = ceil_div(ceil_div(M, want), GRS) * GRS;
   if (rpc < GRS) rpc = GRS;
@@ -255,9 +257,14 @@ cudaError_t gram_reduce_launch(const double* partial, int nchunk, int n, int kc,
 }
 
 cudaError_t update_simt_launch(const PanelF32& p, const float* T, int k1, float* Unew, int64_t ldo,
-                               cudaStream_t st) {
-  dim3 grid((unsigned)ceil_div(p.M, UR), (unsigned)ceil_div(k1, UC));
-  update_kernel<<<grid, 256, 0, st>>>(p, T, k1, Unew, ldo);
+                               cudaStream_t st, int tile_rows) {
+  if (tile_rows == 64) {
+    dim3 grid((unsigned)ceil_div(p.M, 64), (unsigned)ceil_div(k1, UC));
+    update_kernel<2><<<grid, 256, 0, st>>>(p, T, k1, Unew, ldo);
+  } else {
+    dim3 grid((unsigned)ceil_div(p.M, 128), (unsigned)ceil_div(k1, UC));
+    update_kernel<4><<<grid, 256, 0, st>>>(p, T, k1, Unew, ldo);
+  }
   return cudaGetLastError();
 }
 

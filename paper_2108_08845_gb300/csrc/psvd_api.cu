@@ -12,7 +12,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "psvd_internal.cuh"
@@ -49,6 +52,7 @@ struct psvd_ctx {
   float* Uf32_tmp = nullptr;  // FP32 view of hi/lo modes for get_modes / save
   ApmosCache* apmos = nullptr;  // psvd_parallel_svd workspaces and streams (lazily made)
   AdjWork* adj = nullptr;       // psvd_update_adjoint workspaces (lazily made)
+  SimtTune tune;                // FP32-path tile choices (psvd_autotune)
   int host_info[4] = {0, 0, 0, 0};
   int sticky_status = 0;
   // per-phase event timing (psvd_set_profiling)
@@ -204,7 +208,7 @@ int panel_gram(psvd_ctx* h, const void* A, int64_t lda, int B, int dtype, int kc
   }
   int nchunk;
   int64_t rpc, pd;
-  gram_simt_plan(h->M, n, h->num_sms, &nchunk, &rpc, &pd);
+  gram_simt_plan(h->M, n, h->num_sms, &nchunk, &rpc, &pd, h->tune.gram_ctas_per_sm);
   if (int rc = ensure_partial(h, pd)) return rc;
   if (use_f64(h)) {
     PanelF64 p{h->U64[h->cur], h->ldu, kc, A, lda, dtype, h->M, n};
@@ -259,7 +263,7 @@ int step(psvd_ctx* h, const void* A, int64_t lda, int B, int dtype) {
     CK(update_f64_launch(p, w.T64, k1, h->U64[h->cur ^ 1], h->ldu, h->st));
   } else {
     PanelF32 p{h->U[h->cur], h->ldu, kc, A, lda, dtype == PSVD_BF16 ? 1 : 0, h->M, n};
-    CK(update_simt_launch(p, T, k1, h->U[h->cur ^ 1], h->ldu, h->st));
+    CK(update_simt_launch(p, T, k1, h->U[h->cur ^ 1], h->ldu, h->st, h->tune.update_rows));
   }
   prof_end(h, pr);
   h->launches += use_tc(h) ? 2 : 1;
@@ -292,6 +296,34 @@ int collect_status(psvd_ctx* h) {
   return PSVD_OK;
 }
 
+}  // namespace
+
+// Autotuner helpers (psvd_autotune).
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int64_t, int, int, int>, SimtTune> g_tune_cache;  // (M, n, dtype, SMs)
+
+// Mean time of `reps` launches of fn on st (after one warm-up launch), in ms.
+template <typename F>
+int time_ms(cudaStream_t st, int reps, F fn, float* ms) {
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess) return PSVD_ERR_CUDA;
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return PSVD_ERR_CUDA;
+  }
+  int rc = fn();
+  if (rc == PSVD_OK && cudaEventRecord(a, st) != cudaSuccess) rc = PSVD_ERR_CUDA;
+  for (int i = 0; rc == PSVD_OK && i < reps; ++i) rc = fn();
+  if (rc == PSVD_OK && cudaEventRecord(b, st) != cudaSuccess) rc = PSVD_ERR_CUDA;
+  if (rc == PSVD_OK && cudaEventSynchronize(b) != cudaSuccess) rc = PSVD_ERR_CUDA;
+  float t = 0.f;
+  if (rc == PSVD_OK && cudaEventElapsedTime(&t, a, b) != cudaSuccess) rc = PSVD_ERR_CUDA;
+  *ms = t / reps;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return rc;
+}
 }  // namespace
 
 extern "C" {
@@ -728,7 +760,7 @@ int group_step(psvd_group* g, const void* const* A, int64_t lda, int32_t B, int3
         psvd_handle h = g->m[i];
         int nchunk;
         int64_t rpc, pd;
-        gram_simt_plan(h->M, h->kc + B, h->num_sms, &nchunk, &rpc, &pd);
+        gram_simt_plan(h->M, h->kc + B, h->num_sms, &nchunk, &rpc, &pd, h->tune.gram_ctas_per_sm);
         if (int rc = ensure_partial(h, pd)) return rc;
       }
       struct Saved {
@@ -857,6 +889,89 @@ int psvd_group_status(psvd_group_handle g) {
     if (worst >= 0 && rc > worst) worst = rc;
   }
   return worst;
+}
+
+// ---------------------------------------------------------------- autotuner
+
+int psvd_autotune(psvd_handle h, const void* A, int64_t lda, int32_t B, int32_t dtype,
+                  int32_t* choice) {
+  if (!h) return PSVD_ERR_INVALID_ARG;
+  if (h->cfg.precision != PSVD_PREC_FP32) return PSVD_ERR_UNSUPPORTED;
+  if (!A || B < 1 || B > h->maxB || lda < h->M || (dtype != PSVD_F32 && dtype != PSVD_BF16))
+    return PSVD_ERR_INVALID_ARG;
+  if (!is_device_ptr(A)) return PSVD_ERR_INVALID_ARG;
+  const int n = h->K + B;  // the steady-state panel
+  if (h->M < n) return PSVD_ERR_SHAPE;
+  const auto key = std::make_tuple(h->M, n, (int)dtype, h->num_sms);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      h->tune = it->second;
+      if (choice) {
+        choice[0] = h->tune.gram_ctas_per_sm;
+        choice[1] = h->tune.update_rows;
+      }
+      return PSVD_OK;
+    }
+  }
+  // the trials read the current modes and write only scratch: the other mode
+  // buffer (free between steps), the Gram partials, w.H and the status word, which
+  // is saved here and restored afterwards
+  int saved_info[4];
+  CK(cudaMemcpyAsync(saved_info, h->w.info, sizeof(saved_info), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  PanelF32 p{h->U[h->cur], h->ldu, h->K, A, lda, dtype == PSVD_BF16 ? 1 : 0, h->M, n};
+  SimtTune best;
+  float best_ms = 1e30f;
+  static const int kCps[] = {1, 2, 4, 8};
+  for (int cps : kCps) {
+    int nchunk;
+    int64_t rpc, pd;
+    gram_simt_plan(h->M, n, h->num_sms, &nchunk, &rpc, &pd, cps);
+    if (int rc = ensure_partial(h, pd)) return rc;
+    float ms = 0.f;
+    int rc = time_ms(h->st, 3, [&]() -> int {
+      if (gram_simt_launch(p, nchunk, rpc, h->partial, h->st) != cudaSuccess) return PSVD_ERR_CUDA;
+      if (gram_reduce_launch(h->partial, nchunk, n, h->K, h->D[h->cur], 1.0, nullptr, h->w.H,
+                             h->w.info, h->st) != cudaSuccess)
+        return PSVD_ERR_CUDA;
+      return PSVD_OK;
+    }, &ms);
+    if (rc) return rc;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best.gram_ctas_per_sm = cps;
+    }
+  }
+  best_ms = 1e30f;
+  static const int kRows[] = {64, 128};
+  for (int rows : kRows) {
+    float ms = 0.f;
+    int rc = time_ms(h->st, 3, [&]() -> int {
+      return update_simt_launch(p, h->w.T, h->K, h->U[h->cur ^ 1], h->ldu, h->st, rows) ==
+                     cudaSuccess
+                 ? PSVD_OK
+                 : PSVD_ERR_CUDA;
+    }, &ms);
+    if (rc) return rc;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best.update_rows = rows;
+    }
+  }
+  CK(cudaMemcpyAsync(h->w.info, saved_info, sizeof(saved_info), cudaMemcpyHostToDevice, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  h->tune = best;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best;
+  }
+  if (choice) {
+    choice[0] = best.gram_ctas_per_sm;
+    choice[1] = best.update_rows;
+  }
+  return PSVD_OK;
 }
 
 int psvd_set_profiling(psvd_handle h, int32_t enable) {

@@ -35,9 +35,10 @@ struct PanelF32 {
   int n;  // kc + B
 };
 
-// Number of row chunks and partial-buffer doubles used by gram_simt for a panel.
+// Number of row chunks and partial-buffer doubles used by gram_simt for a panel,
+// sized for about ctas_per_sm resident CTAs per SM over the Gram's 64 x 64 blocks.
 void gram_simt_plan(int64_t M, int n, int num_sms, int* nchunk, int64_t* rows_per_chunk,
-                    int64_t* partial_doubles);
+                    int64_t* partial_doubles, int ctas_per_sm = 4);
 // Partial Grams of the panel over row chunks (FP64 per chunk, float-float inside).
 cudaError_t gram_simt_launch(const PanelF32& p, int nchunk, int64_t rows_per_chunk,
                              double* partial, cudaStream_t st);
@@ -46,9 +47,16 @@ cudaError_t gram_simt_launch(const PanelF32& p, int nchunk, int64_t rows_per_chu
 cudaError_t gram_reduce_launch(const double* partial, int nchunk, int n, int kc,
                                const double* D, double ff, double* G, double* H, int* info,
                                cudaStream_t st);
-// Unew (M x k1, ldo) = [U | A] * T (n x k1, FP32, ldt = n).
+// Unew (M x k1, ldo) = [U | A] * T (n x k1, FP32, ldt = n), in tiles of tile_rows
+// (64 or 128) rows by 64 columns.
 cudaError_t update_simt_launch(const PanelF32& p, const float* T, int k1, float* Unew,
-                               int64_t ldo, cudaStream_t st);
+                               int64_t ldo, cudaStream_t st, int tile_rows = 128);
+
+// Tile choices of the FP32 path (psvd_autotune picks them per panel shape).
+struct SimtTune {
+  int gram_ctas_per_sm = 4;
+  int update_rows = 128;
+};
 
 // ---------------------------------------------------------------- FP64 SIMT path
 // Panel [U | A]: U is M x kc FP64 (ldu), A is M x B (lda) of psvd_dtype a_dtype.

@@ -104,6 +104,7 @@ def load(build_if_missing: bool = True):
         lib.psvd_group_member.restype = vp
         lib.psvd_group_status.argtypes = [vp]
         lib.psvd_group_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+        lib.psvd_autotune.argtypes = [vp, vp, i64, i32, i32, C.POINTER(C.c_int32)]
         lib.psvd_set_profiling.argtypes = [vp, i32]
         lib.psvd_get_profile.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                          C.POINTER(C.c_int64)]
@@ -299,6 +300,15 @@ def psvd_update_adjoint(h: int, U, D, A, U_new, D_new, U_new_bar, D_new_bar, U_b
                                     db, ubar, ldub, dbar, ab, ldab)
     del keep
     return _check(rc, "psvd_update_adjoint")
+
+
+def psvd_autotune(h: int, A):
+    """Times the FP32 path's tile choices on the representative device batch A and keeps
+    the fastest; returns (Gram CTAs per SM, update tile rows)."""
+    p, ld, _, B, code, _keep = _mat(A, "A")
+    ch = (C.c_int32 * 2)()
+    _check(load().psvd_autotune(h, p, ld, B, code, ch), "psvd_autotune")
+    return int(ch[0]), int(ch[1])
 
 
 def psvd_last_info(h: int):
