@@ -246,6 +246,60 @@ def rsvd_run(batches, K, ff, p, q, seed):
     return U, D
 
 
+# Philox stream of the sketch of the literal low_rank_svd(W) in Algorithm 2 (an
+# identifier that no batch index of the streaming sketches reaches)
+APMOS_SKETCH_STREAM = 0x41504D4F53
+
+
+def apmos_local_factors(A, offsets, r1, max_sweeps=MAX_SWEEPS, tol=JACOBI_TOL):
+    """Algorithm 2's local step: for every row block A_b, the thin SVD (Householder QR,
+    then one-sided Jacobi on R) and its leading r1 right factors W_b = V_b diag(s_b),
+    each column signed so that its entries sum to >= 0.  Returns W (N x r1*nparts)."""
+    A = _f64(A)
+    off = np.asarray(offsets, dtype=np.int64)
+    cols = []
+    for b in range(off.shape[0] - 1):
+        _, R = householder_qr(A[off[b]:off[b + 1], :])
+        _, s, V, _ = jacobi_svd(R)
+        Wb = V[:, :r1] * s[None, :r1]
+        sg = np.where(Wb.sum(axis=0) >= 0, 1.0, -1.0)
+        cols.append(Wb * sg[None, :])
+    return np.concatenate(cols, axis=1)
+
+
+def rsvd_wide(W, k, Omega, q, max_sweeps=MAX_SWEEPS, tol=JACOBI_TOL):
+    """Randomized rank-k SVD of any N x m matrix W (Halko, Martinsson & Tropp, Alg. 4.4):
+    Y = W Omega, Q = orth(Y); q times: Q^ = orth(W^T Q), Q = orth(W Q^); B = Q^T W;
+    the left singular vectors of B (Jacobi SVD of B^T) give X = Q U_B.  orth() is the
+    oracle's Householder QR.  Returns (X N x k, s k)."""
+    W = _f64(W)
+    Q, _ = householder_qr(W @ _f64(Omega))
+    for _ in range(int(q)):
+        Qh, _ = householder_qr(W.T @ Q)
+        Q, _ = householder_qr(W @ Qh)
+    B = Q.T @ W
+    _, s, Vb, _ = jacobi_svd(B.T)  # B^T Vb = Ub diag(s): B's left vectors are Vb
+    return Q @ Vb[:, :k], s[:k].copy()
+
+
+def apmos_low_rank(A, offsets, r1, r2, p, q, seed, max_sweeps=MAX_SWEEPS, tol=JACOBI_TOL):
+    """Algorithm 2 with the paper's low_rank_svd on the gathered W (Listing 3 with
+    low_rank set): W = [W_0 ... W_{nparts-1}] (N x m, m = r1 nparts), then the
+    randomized SVD of W (Halko, Martinsson & Tropp, Alg. 4.4) with the Gaussian test
+    matrix Omega (m x l, l = min(r2 + p, N), stream APMOS_SKETCH_STREAM of the seed)
+    and q power steps gives X~ (N x r2) and L~; U = A X~ diag(1/L~) (zero where
+    L~ = 0).  Returns (U m x r2, L~)."""
+    A = _f64(A)
+    W = apmos_local_factors(A, offsets, r1, max_sweeps, tol)
+    N, m = W.shape
+    l = min(r2 + p, N, m)
+    Om = gaussian_matrix(seed, APMOS_SKETCH_STREAM, m, l)
+    X, L = rsvd_wide(W, r2, Om, q, max_sweeps, tol)
+    inv = np.zeros_like(L)
+    inv[L > 0] = 1.0 / L[L > 0]
+    return A @ (X * inv[None, :]), L
+
+
 def philox4x32(ctr, key, rounds=10):
     lib = _load()
     c = (C.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in ctr])
