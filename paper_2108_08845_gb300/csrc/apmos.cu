@@ -15,6 +15,7 @@
 // result does not depend on which lane finished first.
 #include <stdint.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -42,6 +43,28 @@ __global__ void wwt_kernel(int N, int r1, int nparts, const double* __restrict__
     }
   }
   WW[e] = acc;
+}
+
+// The gathered W (N x m, m = r1 nparts): column (b, k) = +-V_b[:, k] s_bk =
+// +-T64_b[:, k] s_bk^2, signed so that its entries sum to >= 0.  One warp per column.
+__global__ void wide_w_kernel(int N, int r1, int nparts, const double* __restrict__ T64,
+                              const double* __restrict__ sigma, double* __restrict__ W) {
+  const int c = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x % 32;
+  if (c >= r1 * nparts) return;
+  const int b = c / r1, k = c % r1;
+  const double* col = T64 + (size_t)b * N * r1 + (size_t)k * N;
+  double sum = 0.0;
+  for (int i = lane; i < N; i += 32) sum += col[i];
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  const double sk = sigma[(size_t)b * r1 + k];
+  const double scale = (sum >= 0.0 ? 1.0 : -1.0) * sk * sk;
+  for (int i = lane; i < N; i += 32) W[i + (size_t)c * N] = col[i] * scale;
+}
+
+__global__ void to_f32_kernel(const double* __restrict__ x, int64_t count, float* __restrict__ y) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < count) y[e] = (float)x[e];
 }
 
 // OR of the lanes' status words into info[2].
@@ -91,6 +114,12 @@ struct ApmosCache {
   Lane lane[kLanes];
   Grow<int> lane_info;
   Grow<double> T64_all, S_all, WW;
+  // the randomized global SVD (low_rank): explicit W, X diag(1/s), RandWork arrays
+  Grow<double> Wexp, Tout, rB0, rB1, rB2, rMm, rRr, rAw, rBb;
+  Grow<float> rOm;
+  Grow<int> rpiv, rrank;
+  int low_rank = 0, p = 0, q = 0;  // this call's settings (read by apmos_enqueue)
+  uint64_t seed = 0;
   cudaEvent_t fork = nullptr;
   // the sequence is captured and replayed on this stream (capture cannot start
   // on the legacy default stream); it is ordered after and before the caller's
@@ -121,8 +150,13 @@ void apmos_cache_destroy(ApmosCache* c) { delete c; }
 
 int apmos_run(const void* A, int64_t lda, int a_bf16, int64_t Mtot, const int64_t* off, int nparts,
               int N, int r1, int r2, float* U, int64_t ldu, double* L, int num_sms,
-              cudaStream_t st, ApmosCache* c, int* status) {
+              cudaStream_t st, ApmosCache* c, int low_rank, int p, int q, uint64_t seed,
+              int* status) {
   if (!c) return PSVD_ERR_INVALID_ARG;
+  c->low_rank = low_rank ? 1 : 0;
+  c->p = p;
+  c->q = q;
+  c->seed = seed;
   const size_t es = a_bf16 ? 2 : 4;
   const size_t nn = (size_t)N * N;
   const int nlanes = nparts < kLanes ? nparts : kLanes;
@@ -165,6 +199,14 @@ int apmos_run(const void* A, int64_t lda, int a_bf16, int64_t Mtot, const int64_
     w.ls = ln.ls.p;
     w.fs = ln.fs.p;
   }
+  if (ok && c->low_rank) {
+    const size_t m = (size_t)r1 * nparts, lmax = (size_t)N;
+    ok = c->Wexp.ensure((size_t)N * m) && c->Tout.ensure((size_t)N * r2) &&
+         c->rB0.ensure(std::max(m, (size_t)N) * lmax) && c->rB1.ensure((size_t)N * lmax) &&
+         c->rB2.ensure((size_t)N * lmax) && c->rMm.ensure(lmax * lmax) &&
+         c->rRr.ensure(lmax * lmax) && c->rAw.ensure(lmax * lmax) && c->rBb.ensure(lmax * lmax) &&
+         c->rOm.ensure(m * lmax) && c->rpiv.ensure(lmax) && c->rrank.ensure(1);
+  }
   if (ok && !c->fork) ok = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) == cudaSuccess;
   if (ok && !c->origin) ok = cudaStreamCreateWithFlags(&c->origin, cudaStreamNonBlocking) == cudaSuccess;
   if (ok && !c->in) ok = cudaEventCreateWithFlags(&c->in, cudaEventDisableTiming) == cudaSuccess;
@@ -189,6 +231,13 @@ int apmos_run(const void* A, int64_t lda, int a_bf16, int64_t Mtot, const int64_
                               (int64_t)(uintptr_t)T64_all, (int64_t)(uintptr_t)WW};
   for (int b = 0; b <= nparts; ++b) key.push_back(off[b]);
   for (int l = 0; l < nlanes; ++l) key.push_back((int64_t)(uintptr_t)c->lane[l].partial.p);
+  key.push_back(c->low_rank);
+  if (c->low_rank) {
+    for (int64_t v : {(int64_t)c->p, (int64_t)c->q, (int64_t)c->seed,
+                      (int64_t)(uintptr_t)c->Wexp.p, (int64_t)(uintptr_t)c->rB0.p,
+                      (int64_t)(uintptr_t)c->rOm.p})
+      key.push_back(v);
+  }
   // origin runs after the work already on st
   cudaStream_t o = c->origin;
   ACK(cudaEventRecord(c->in, st));
@@ -280,10 +329,35 @@ int apmos_enqueue(ApmosCache* c, const std::vector<SmallWork>& lw, int nlanes, c
   ACK(cudaGetLastError());
   merge_info_kernel<<<1, 1, 0, st>>>(lane_info, nlanes, lane_info);
   ACK(cudaGetLastError());
-  // global: eigen-decomposition of W W^T, T = X~ diag(1/L~), U = A T
-  ACK(cudaMemcpyAsync(w.H, WW, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st));
-  ACK(small_solve_launch(w, N, 0, r2, nullptr, 1.0, 3, kMaxLevels, st, &nl));
   PanelF32 pa{nullptr, 0, 0, A, lda, a_bf16, Mtot, N};
+  if (c->low_rank) {
+    // global: the paper's low_rank_svd of the explicit W, T = X~ diag(1/L~), U = A T
+    const int m = r1 * nparts;
+    const int l = std::min(std::min(r2 + c->p, N), m);
+    wide_w_kernel<<<(unsigned)ceil_div(m, 8), 256, 0, st>>>(N, r1, nparts, T64_all, S_all,
+                                                            c->Wexp.p);
+    ACK(cudaGetLastError());
+    RandWork rw{};
+    rw.Om = c->rOm.p;
+    rw.B[0] = c->rB0.p;
+    rw.B[1] = c->rB1.p;
+    rw.B[2] = c->rB2.p;
+    rw.Mm = c->rMm.p;
+    rw.Rr = c->rRr.p;
+    rw.Aw = c->rAw.p;
+    rw.piv = c->rpiv.p;
+    rw.rank = c->rrank.p;
+    rw.Bb = c->rBb.p;
+    ACK(randomized_wide_launch(rw, w, c->Wexp.p, WW, N, m, r2, l, c->q, c->seed,
+                               kApmosSketchStream, c->Tout.p, st, &nl));
+    const int64_t cnt = (int64_t)N * r2;
+    to_f32_kernel<<<(unsigned)ceil_div(cnt, 256), 256, 0, st>>>(c->Tout.p, cnt, w.T);
+    ACK(cudaGetLastError());
+  } else {
+    // global: eigen-decomposition of W W^T, T = X~ diag(1/L~), U = A T
+    ACK(cudaMemcpyAsync(w.H, WW, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st));
+    ACK(small_solve_launch(w, N, 0, r2, nullptr, 1.0, 3, kMaxLevels, st, &nl));
+  }
   ACK(update_simt_launch(pa, w.T, r2, U, ldu, st));
   ACK(cudaMemcpyAsync(L, w.Dnew, sizeof(double) * r2, cudaMemcpyDeviceToDevice, st));
 #undef ACK

@@ -614,7 +614,9 @@ int psvd_parallel_svd(psvd_handle h, const void* A, int64_t lda, const int64_t* 
   int bits = 0;
   if (!h->apmos) h->apmos = apmos_cache_create();
   int rc = h->apmos ? apmos_run(Ad, ldd, dtype == PSVD_BF16 ? 1 : 0, Mtot, part_offsets, nparts, N,
-                                r1, r2, Ud, ldud, Ld, h->num_sms, h->st, h->apmos, &bits)
+                                r1, r2, Ud, ldud, Ld, h->num_sms, h->st, h->apmos,
+                                h->cfg.low_rank, h->cfg.oversample, h->cfg.power_iters,
+                                h->cfg.seed, &bits)
                     : PSVD_ERR_ALLOC;
   if (rc == PSVD_OK && !u_dev &&
       cudaMemcpy2DAsync(U_out, sizeof(float) * ldu, Ud, sizeof(float) * ldud, sizeof(float) * Mtot,

@@ -166,6 +166,19 @@ cudaError_t randomized_solve_launch(const RandWork& r, const SmallWork& w, int n
                                     int l, int q, const double* D, double ff, uint64_t seed,
                                     uint64_t sketch_id, cudaStream_t st, int* launches);
 
+// Randomized rank-k SVD of an explicit N x m FP64 matrix W (N <= 192, any m):
+// Halko, Martinsson & Tropp Alg. 4.4 with the Gaussian sketch Omega (m x l, Philox
+// stream sketch_id of seed), Y = W Omega, Q = orth(Y) and q power steps written
+// through WW = W W^T (N x N FP64; span(W W^T Q) = span(W orth(W^T Q))), then the
+// eigen-solve of Q^T W W^T Q (l x l).  Outputs Tout (N x k FP64, ld N) =
+// X diag(1/s) with X = Q U_B the left singular vectors, w.Dnew = s (k); w.T64 (l x k)
+// is scratch.  r.Om holds m x l floats and r.B[0] m x l doubles; r.B[1], r.B[2]
+// N x l; r.Mm, r.Rr, r.Aw, r.Bb l x l.
+cudaError_t randomized_wide_launch(const RandWork& r, const SmallWork& w, const double* W,
+                                   const double* WW, int N, int m, int k, int l, int q,
+                                   uint64_t seed, uint64_t sketch_id, double* Tout,
+                                   cudaStream_t st, int* launches);
+
 // ------------------------------------------------------------------- APMOS
 // Algorithm 2 on device data: A (Mtot x N, lda, FP32 or BF16) in row blocks
 // [off[b], off[b+1]) (host array), r1 local and r2 global modes; U (Mtot x r2,
@@ -175,9 +188,15 @@ cudaError_t randomized_solve_launch(const RandWork& r, const SmallWork& w, int n
 struct ApmosCache;
 ApmosCache* apmos_cache_create();
 void apmos_cache_destroy(ApmosCache* c);
+// With low_rank set, the global SVD of the gathered W = [V_b S_b] is the paper's
+// low_rank_svd: randomized, l = min(r2 + p, N, r1 nparts) sketch columns from the
+// Philox stream kApmosSketchStream of seed, q power steps; each local factor
+// column is signed so that its entries sum to >= 0 (the sketch depends on signs).
+constexpr uint64_t kApmosSketchStream = 0x41504D4F53ull;
 int apmos_run(const void* A, int64_t lda, int a_bf16, int64_t Mtot, const int64_t* off, int nparts,
               int N, int r1, int r2, float* U, int64_t ldu, double* L, int num_sms,
-              cudaStream_t st, ApmosCache* cache, int* status);
+              cudaStream_t st, ApmosCache* cache, int low_rank, int p, int q, uint64_t seed,
+              int* status);
 
 // ------------------------------------------------------------------ adjoint
 // Reverse-mode derivative of one update of Algorithm 1 (adjoint.cu).  Inputs: the

@@ -277,4 +277,43 @@ cudaError_t randomized_solve_launch(const RandWork& r, const SmallWork& w, int n
   return cudaSuccess;
 }
 
+cudaError_t randomized_wide_launch(const RandWork& r, const SmallWork& w, const double* W,
+                                   const double* WW, int N, int m, int k, int l, int q,
+                                   uint64_t seed, uint64_t sketch_id, double* Tout,
+                                   cudaStream_t st, int* launches) {
+  int nl = 0;
+  const int64_t mlc = (int64_t)m * l;
+  double* B0 = r.B[0];  // m x l: the widened sketch, then n x l scratch
+  double* B1 = r.B[1];  // N x l: Q
+  double* B2 = r.B[2];  // N x l: products with W W^T
+  RCK(gaussian_sketch_launch(seed, sketch_id, m, l, r.Om, st));
+  widen_kernel<<<blocks_for(mlc, 256), 256, 0, st>>>(r.Om, mlc, B0);
+  RCK(cudaGetLastError());
+  // Y = W Omega, Q = orth(Y)
+  RCK(dgemm_launch(false, N, l, m, 1.0, W, N, B0, m, 0.0, nullptr, N, B1, N, st));
+  nl += 3;
+  RCK(e_orth(r, N, l, B1, B2, B1, st, &nl));
+  // power steps: span(W W^T Q) is span(W Q^) with Q^ = orth(W^T Q)
+  for (int it = 0; it < q; ++it) {
+    RCK(dgemm_launch(false, N, l, N, 1.0, WW, N, B1, N, 0.0, nullptr, N, B2, N, st));
+    nl += 1;
+    RCK(e_orth(r, N, l, B2, B0, B1, st, &nl));
+  }
+  // B B^T = Q^T W W^T Q (l x l)
+  RCK(dgemm_launch(false, N, l, N, 1.0, WW, N, B1, N, 0.0, nullptr, N, B2, N, st));
+  RCK(dgemm_launch(true, l, l, N, 1.0, B1, N, B2, N, 0.0, nullptr, l, r.Bb, l, st));
+  nl += 2;
+  // B B^T = U_B diag(s^2) U_B^T: w.T64 = U_B[:, :k] diag(1/s), w.Dnew = s
+  SmallWork wb = w;
+  wb.H = r.Bb;
+  int ns = 0;
+  RCK(small_solve_launch(wb, l, 0, k, nullptr, 1.0, /*refine_steps=*/3, kMaxLevels, st, &ns));
+  nl += ns;
+  // X diag(1/s) = Q U_B[:, :k] diag(1/s)
+  RCK(dgemm_launch(false, N, k, l, 1.0, B1, N, w.T64, l, 0.0, nullptr, N, Tout, N, st));
+  nl += 1;
+  *launches = nl;
+  return cudaSuccess;
+}
+
 }  // namespace psvd

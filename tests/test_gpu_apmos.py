@@ -143,3 +143,32 @@ def test_apmos_many_partitions_concurrent_lanes():
     assert np.array_equal(U1, U2) and np.array_equal(L1, L2)
     Uo, Lo = oracle.apmos(A.double().numpy(), off, 16, 12)
     _compare(U1, L1, Uo, Lo, k=10)
+
+
+@pytest.mark.parametrize("p,q", [(6, 0), (2, 1)])
+def test_apmos_low_rank_svd_of_w_matches_oracle(p, q):
+    # the paper's literal placement: low_rank_svd on the gathered W (Listing 3 with
+    # low_rank set).  8 uneven blocks, N = 48 snapshots of a full-rank 1.15^-i
+    # spectrum, r1 = 10 (W is 48 x 80 of rank 48), r2 = 10 with a 16- or 12-column
+    # sketch (q = 0: a genuine approximation, 3.7e-4 from the exact APMOS; q = 1: the
+    # power step), compared with the oracle run on the same Philox sketch and the
+    # same sign convention for the local factors
+    sizes = synthetic.partition_sizes(8, 2000, 6000, seed=1241)
+    off = _offsets(sizes)
+    N, r1, r2, seed = 48, 10, 10, 99
+    A, *_ = synthetic.spectrum(int(off[-1]), N, [1.15 ** -i for i in range(N)], 1242)
+    A = synthetic.to_storage(A, torch.float32)
+    Mtot = int(off[-1])
+    h = psvd.psvd_create(Mtot, 8, 8, 1.0, psvd.PSVD_PREC_FP32, low_rank=1, oversample=p,
+                         power_iters=q, seed=seed)
+    U = torch.zeros((r2, Mtot), dtype=torch.float32, device="cuda").T
+    L = torch.zeros(r2, dtype=torch.float64, device="cuda")
+    rc = psvd.psvd_parallel_svd(h, A.cuda(), off, r1, r2, U, L)
+    psvd.psvd_destroy(h)
+    assert rc == psvd.PSVD_OK
+    Uo, Lo = oracle.apmos_low_rank(A.double().numpy(), off, r1, r2, p, q, seed)
+    _compare(U.cpu().double().numpy(), L.cpu().numpy(), Uo, Lo, k=6)
+    if q == 0:
+        # an approximation: the exact APMOS differs beyond rounding
+        Le = oracle.apmos(A.double().numpy(), off, r1, r2)[1]
+        assert np.abs(Lo / Le - 1).max() > 1e-5
