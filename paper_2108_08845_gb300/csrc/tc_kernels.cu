@@ -53,11 +53,13 @@ constexpr int kGramSubs = 2;
 // (K = 64, B = 128) stays within 5.3e-4 rad of the FP64 result (2.2e-3 with 16).
 // One slot (128 rows) is 8 MMAs.
 constexpr int kFoldStages = 1;
-// Gram CTA: warp 0 issues TMA loads, warp 1 issues MMAs, warps 2-3 only take part
-// in the CTA barriers, warps 4-11 drain TMEM (two per lane quadrant).  Twelve warps,
-// three per SM sub-partition, cap the registers at 168 per thread.
-constexpr int kGramEpiWarp0 = 4;
-constexpr int kGramThreads = (kGramEpiWarp0 + 8) * 32;
+// Gram CTA: warp 0 issues TMA loads, warp 1 issues MMAs, warps 2-17 drain TMEM
+// (warp w reads lane quadrant w % 4; four warps per quadrant, 32 columns each,
+// their float-float sums in registers).  Eighteen warps cap the registers at 112
+// per thread.
+constexpr int kGramEpiWarp0 = 2;
+constexpr int kGramEpiWarps = 16;
+constexpr int kGramThreads = (kGramEpiWarp0 + kGramEpiWarps) * 32;
 constexpr int kUpdRows = 128;             // rows per update tile (UMMA M)
 constexpr int kUpdStages = 2;
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
@@ -373,7 +375,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) tc_gram_kernel(const __grid_c
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], 8);
+      mbar_init(&acc_empty[b], kGramEpiWarps);
     }
     mbar_init(mma_done, 1);
     *abort_flag = 0;
@@ -488,21 +490,15 @@ __global__ void __launch_bounds__(kGramThreads, 1) tc_gram_kernel(const __grid_c
     }
   } else if (warp >= kGramEpiWarp0) {
     // ------------------------------------------------------------- epilogue
-    // Warps 4 .. 11: TMEM lane quadrant q = warp % 4 (block rows 32q .. 32q+31),
-    // column half ch (columns 64 ch .. 64 ch + 63).  The running hi sums live in
-    // registers, the lo sums in TMEM (columns 256 + 64 ch ..).  In a diagonal block
-    // a 32-column chunk wholly below the diagonal of the quadrant is skipped (the
-    // assembly reads the mirror entry).
+    // Warps 2 .. 17: TMEM lane quadrant q = warp % 4 (block rows 32q .. 32q+31),
+    // column chunk ch (columns 32 ch .. 32 ch + 31).  The running float-float sums
+    // (hi, lo) live in registers.  In a diagonal block a chunk wholly below the
+    // diagonal of the quadrant is skipped (the assembly reads the mirror entry).
     const int q = warp & 3, ch = (warp - kGramEpiWarp0) >> 2;
     const uint32_t lane_base = tmem_base + ((uint32_t)(q * 32) << 16);
-    const uint32_t t_lo = lane_base + 2 * kSlab + (uint32_t)(64 * ch);
-    bool need[2];
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const int c0 = 64 * ch + 32 * c;
-      need[c] = c0 < w && (!diag || c0 + 32 > 32 * q);
-    }
-    float hi[64];
+    const int c0 = 32 * ch;
+    const bool need = c0 < w && (!diag || c0 + 32 > 32 * q);
+    float hi[32], lo[32];
     bool ok = true;
     for (int f = 0; f < nfold; ++f) {
       const int b = f & 1;
@@ -512,53 +508,34 @@ __global__ void __launch_bounds__(kGramThreads, 1) tc_gram_kernel(const __grid_c
         break;
       }
       tc_fence_after();
-      // four 16-column pieces; the loads of piece p + 1 are in flight while piece p
-      // is folded (tcgen05.wait::ld waits for all of this thread's loads)
-      const int p_lo = need[0] ? 0 : 2, p_hi = need[1] ? 4 : 2;
-      uint32_t a[2][16], l[2][16];
+      if (need) {
+        // two 16-column pieces, one in registers at a time (the sums take 64)
 #pragma unroll
-      for (int p = 0; p < 4; ++p) {
-        if (p < p_lo || p >= p_hi) continue;
-        if (p == p_lo) {
-          tmem_ld16_nowait(lane_base + (uint32_t)(b * kSlab + 64 * ch + 16 * p), a[p & 1]);
-          if (f > 0) tmem_ld16_nowait(t_lo + 16 * p, l[p & 1]);
+        for (int p = 0; p < 2; ++p) {
+          uint32_t a[16];
+          tmem_ld16_nowait(lane_base + (uint32_t)(b * kSlab + c0 + 16 * p), a);
           tmem_wait_ld();
-        }
-        if (p + 1 < p_hi) {
-          tmem_ld16_nowait(lane_base + (uint32_t)(b * kSlab + 64 * ch + 16 * (p + 1)), a[(p + 1) & 1]);
-          if (f > 0) tmem_ld16_nowait(t_lo + 16 * (p + 1), l[(p + 1) & 1]);
-        }
-        float fl[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          if (f == 0) {
-            hi[16 * p + i] = __uint_as_float(a[p & 1][i]);
-            fl[i] = 0.f;
-          } else {
-            fl[i] = __uint_as_float(l[p & 1][i]);
-            fold(hi[16 * p + i], fl[i], __uint_as_float(a[p & 1][i]));
+          for (int i = 0; i < 16; ++i) {
+            const float x = __uint_as_float(a[i]);
+            if (f == 0) {
+              hi[16 * p + i] = x;
+              lo[16 * p + i] = 0.f;
+            } else {
+              fold(hi[16 * p + i], lo[16 * p + i], x);
+            }
           }
         }
-        tmem_st16(t_lo + 16 * p, fl);
-        if (p + 1 < p_hi) tmem_wait_ld();
       }
-      tmem_wait_st();
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[b]);
     }
-    if (ok && nfold > 0) {
+    if (ok && nfold > 0 && need) {
       const int row_in_slab = q * 32 + lane;
       double* orow = partial + (((size_t)range * g.npair + pair) * kSlab + row_in_slab) * kSlab;
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        if (!need[c]) continue;
-        float l[32];
-        tmem_ld32(t_lo + 32 * c, l);
-#pragma unroll
-        for (int i = 0; i < 32; ++i)
-          orow[64 * ch + 32 * c + i] = (double)hi[32 * c + i] + (double)l[i];
-      }
+      for (int i = 0; i < 32; ++i) orow[c0 + i] = (double)hi[i] + (double)lo[i];
     }
   }
   tc_fence_before();
