@@ -247,8 +247,10 @@ int step(psvd_ctx* h, const void* A, int64_t lda, int B, int dtype) {
     T = h->rw.Tupd;
   } else {
     // an FP64 Gram resolves eigenvalues down to ~1e-13 lambda_max: up to six
-    // levels of three decades each reach them
-    CK(small_solve_launch(w, n, kc, k1, Dcur, h->cfg.ff, /*refine_steps=*/3,
+    // levels of three decades each reach them.  The refinement converges
+    // quadratically from the levels' ~u32/tau accuracy: two steps reach FP64
+    // rounding for the FP32 and tensor-core Grams, the FP64 path takes three
+    CK(small_solve_launch(w, n, kc, k1, Dcur, h->cfg.ff, use_f64(h) ? 3 : 2,
                           use_f64(h) ? 6 : kMaxLevels, h->st, &nl));
   }
   prof_end(h, pr);
