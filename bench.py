@@ -198,8 +198,8 @@ def run_e2e(psvd, batches, precision, steps, stream):
 # dram__bytes_write.sum) of the current kernel on the M = 524,288 (256 x 2048
 # grid) case of this workload: reads scale with the rows, the partial-block
 # writes do not.
-TC_GRAM_READ_BYTES_PER_ROW = 268831744 / 524288
-TC_GRAM_WRITE_BYTES = 3753728
+TC_GRAM_READ_BYTES_PER_ROW = 269056768 / 524288
+TC_GRAM_WRITE_BYTES = 4101120
 
 
 def roofline(res, precision, hbm_peak, peak_kind):
