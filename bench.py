@@ -294,11 +294,12 @@ def apmos_main(args):
     off = np.asarray(synthetic.offsets(sizes), dtype=np.int64)
     mtot, n, r1, r2 = int(off[-1]), 64, 20, 20
     g = torch.Generator(device="cuda").manual_seed(SEED + 3)
-    # low-rank panel with a graded spectrum 1.15^-i plus noise, built on the device
-    q, _ = torch.linalg.qr(torch.randn(mtot, n, device="cuda", generator=g, dtype=torch.float32))
+    # panel with a graded spectrum close to 1.15^-i plus noise, built on the device
+    # (tall Gaussian columns scaled by 1/sqrt(rows) are orthonormal to ~1/sqrt(rows))
+    q = torch.randn(mtot, n, device="cuda", generator=g, dtype=torch.float32) / mtot ** 0.5
     s = torch.tensor([1.15 ** -i for i in range(n)], device="cuda")
-    v, _ = torch.linalg.qr(torch.randn(n, n, device="cuda", generator=g))
-    A = ((q * s[None, :]) @ v.T + 1e-5 * torch.randn(mtot, n, device="cuda", generator=g))
+    mix = torch.randn(n, n, device="cuda", generator=g) / n ** 0.5
+    A = ((q * s[None, :]) @ mix.T + 1e-5 * torch.randn(mtot, n, device="cuda", generator=g))
     A = A.T.contiguous().T
     h = psvd.psvd_create(mtot, 8, 8, 1.0)
     U = torch.empty((r2, mtot), dtype=torch.float32, device="cuda").T

@@ -67,6 +67,13 @@ __global__ void to_f32_kernel(const double* __restrict__ x, int64_t count, float
   if (e < count) y[e] = (float)x[e];
 }
 
+// The local Grams run nlanes at a time: each is chunked for its share of the SMs
+// (chunking one for the whole GPU multiplies the partials its reduction reads).
+inline int local_sms(int num_sms, int nlanes) {
+  const int s = num_sms / (nlanes > 0 ? nlanes : 1);
+  return s > 0 ? s : 1;
+}
+
 // OR of the lanes' status words into info[2].
 __global__ void merge_info_kernel(const int* __restrict__ lane_info, int nlanes, int* __restrict__ info) {
   int bits = 0;
@@ -164,7 +171,7 @@ int apmos_run(const void* A, int64_t lda, int a_bf16, int64_t Mtot, const int64_
   for (int b = 0; b < nparts; ++b) {
     int nchunk;
     int64_t rpc, pd;
-    gram_simt_plan(off[b + 1] - off[b], N, num_sms, &nchunk, &rpc, &pd);
+    gram_simt_plan(off[b + 1] - off[b], N, local_sms(num_sms, nlanes), &nchunk, &rpc, &pd);
     if (pd > pmax) pmax = pd;
   }
   // growing a buffer frees the old one: nothing may still be using it
@@ -314,7 +321,7 @@ int apmos_enqueue(ApmosCache* c, const std::vector<SmallWork>& lw, int nlanes, c
     PanelF32 p{nullptr, 0, 0, Ab, lda, a_bf16, mb, N};
     int nchunk;
     int64_t rpc, pd;
-    gram_simt_plan(mb, N, num_sms, &nchunk, &rpc, &pd);
+    gram_simt_plan(mb, N, local_sms(num_sms, nlanes), &nchunk, &rpc, &pd);
     ACK(gram_simt_launch(p, nchunk, rpc, ln.partial.p, ln.st));
     ACK(gram_reduce_launch(ln.partial.p, nchunk, N, 0, nullptr, 1.0, nullptr, w.H, w.info, ln.st));
     ACK(small_solve_launch(w, N, 0, r1, nullptr, 1.0, 3, kMaxLevels, ln.st, &nl));

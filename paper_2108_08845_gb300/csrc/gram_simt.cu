@@ -149,14 +149,18 @@ __global__ void gram_reduce_kernel(const double* __restrict__ partial, int nchun
   if (!isfinite(s)) atomicOr(&info[2], 4);
 }
 
-constexpr int UC = 64;   // output columns per update tile
 constexpr int UK = 32;   // panel columns per stage
 
-// Tile of UR = 32 RI rows x UC columns; each thread holds RI rows x 8 columns.
-template <int RI>
-__global__ void __launch_bounds__(256) update_kernel(PanelF32 p, const float* __restrict__ T, int k1,
-                                                     float* __restrict__ Unew, int64_t ldo) {
+// Tile of UR = 32 RI rows x UC = 8 NW columns, NW warps; each thread holds RI rows x 8
+// columns.  Every output element sums the panel columns in the same order whatever
+// the tile, so all tile shapes give the same bits.
+template <int RI, int NW>
+__global__ void __launch_bounds__(32 * NW) update_kernel(PanelF32 p, const float* __restrict__ T,
+                                                         int k1, float* __restrict__ Unew,
+                                                         int64_t ldo) {
   constexpr int UR = 32 * RI;
+  constexpr int UC = 8 * NW;
+  constexpr int NT = 32 * NW;
   __shared__ __align__(16) float Ps[UK * UR];
   __shared__ __align__(16) float Ts[UK * UC];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -170,12 +174,12 @@ __global__ void __launch_bounds__(256) update_kernel(PanelF32 p, const float* __
 
   for (int c0 = 0; c0 < p.n; c0 += UK) {
     __syncthreads();
-    for (int e = tid; e < UK * UR; e += 256) {
+    for (int e = tid; e < UK * UR; e += NT) {
       const int c = e / UR, r = e % UR;
       const int64_t row = r0 + r;
       Ps[e] = (row < p.M && c0 + c < p.n) ? panel_at(p, c0 + c, row) : 0.f;
     }
-    for (int e = tid; e < UK * UC; e += 256) {
+    for (int e = tid; e < UK * UC; e += NT) {
       const int c = e / UC, j = e % UC;
       Ts[e] = (c0 + c < p.n && j0 + j < k1) ? T[(c0 + c) + (int64_t)(j0 + j) * p.n] : 0.f;
     }
@@ -256,15 +260,32 @@ cudaError_t gram_reduce_launch(const double* partial, int nchunk, int n, int kc,
   return cudaGetLastError();
 }
 
+namespace {
+template <int RI, int NW>
+void launch_update(const PanelF32& p, const float* T, int k1, float* Unew, int64_t ldo,
+                   cudaStream_t st) {
+  dim3 grid((unsigned)ceil_div(p.M, 32 * RI), (unsigned)ceil_div(k1, 8 * NW));
+  update_kernel<RI, NW><<<grid, 32 * NW, 0, st>>>(p, T, k1, Unew, ldo);
+}
+template <int RI>
+void launch_update_cols(const PanelF32& p, const float* T, int k1, float* Unew, int64_t ldo,
+                        cudaStream_t st) {
+  // the narrowest tile of 16, 32 or 64 columns that covers k1 (or 64-column tiles)
+  if (k1 <= 16)
+    launch_update<RI, 2>(p, T, k1, Unew, ldo, st);
+  else if (k1 <= 32)
+    launch_update<RI, 4>(p, T, k1, Unew, ldo, st);
+  else
+    launch_update<RI, 8>(p, T, k1, Unew, ldo, st);
+}
+}  // namespace
+
 cudaError_t update_simt_launch(const PanelF32& p, const float* T, int k1, float* Unew, int64_t ldo,
                                cudaStream_t st, int tile_rows) {
-  if (tile_rows == 64) {
-    dim3 grid((unsigned)ceil_div(p.M, 64), (unsigned)ceil_div(k1, UC));
-    update_kernel<2><<<grid, 256, 0, st>>>(p, T, k1, Unew, ldo);
-  } else {
-    dim3 grid((unsigned)ceil_div(p.M, 128), (unsigned)ceil_div(k1, UC));
-    update_kernel<4><<<grid, 256, 0, st>>>(p, T, k1, Unew, ldo);
-  }
+  if (tile_rows == 64)
+    launch_update_cols<2>(p, T, k1, Unew, ldo, st);
+  else
+    launch_update_cols<4>(p, T, k1, Unew, ldo, st);
   return cudaGetLastError();
 }
 

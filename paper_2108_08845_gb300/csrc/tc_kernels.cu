@@ -15,7 +15,7 @@
 //   slot; each slab is read once and multicast to the CTAs whose blocks use it.
 //   Each CTA issues one tcgen05.mma per 16 rows into an FP32 TMEM accumulator;
 //   after every slot the epilogue folds that accumulator into a float-float sum
-//   held in TMEM (Fast2Sum), so FP32 rounding only acts on 8-MMA chains.  The
+//   held in registers (Fast2Sum), so FP32 rounding only acts on 8-MMA chains.  The
 //   cluster blocks are summed in FP64 in a fixed order and Uh/Ul are folded back
 //   into U on the small side.
 // tc_update_kernel: step 4, U_new = [U | A] T.  T (n x k1, FP32) is split
@@ -26,8 +26,9 @@
 //   the three parts, hi/lo split, stores) overlaps the next tile's MMAs.
 //
 // Warp roles (both kernels): warp 0 issues TMA loads, warp 1 allocates TMEM
-// and issues MMAs (one elected thread), warps 2-5 drain TMEM (warp w reads the
-// TMEM lanes 32*(w%4) .. 32*(w%4)+31).  Every mbarrier wait is bounded by a
+// and issues MMAs (one elected thread), the other warps drain TMEM (warp w reads
+// the TMEM lanes 32*(w%4) .. 32*(w%4)+31; the Gram has 16 of them, the update 4).
+// Every mbarrier wait is bounded by a
 // clock budget; on expiry the kernel records an error, stops issuing work,
 // waits (bounded) for its own copies and frees its TMEM before returning.
 #include <cuda.h>
@@ -188,24 +189,8 @@ __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t* r) {
         "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
 }
-// Stores 16 consecutive TMEM columns of this thread's lane (no wait).
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
-      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
-      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
-      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
-      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
-      "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
-      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
-      "r"(__float_as_uint(v[15]))
-      : "memory");
-}
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_wait_st() {
-  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 // 32 consecutive TMEM columns of this thread's lane.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
@@ -337,8 +322,8 @@ __device__ __forceinline__ void load_slab(const PanelMaps& pm, const GramGeom& g
 // that another CTA still reads.
 // TMEM: two FP32 accumulators (columns 0 and 128) alternate between the MMA warp
 // and the epilogue, which folds each finished 128-row partial into a float-float
-// running sum (hi at column 256, lo at 384).  The block is written as FP64
-// (hi + lo) to partial[range][pair][128][128].
+// running sum held in the draining warps' registers.  The block is written as
+// FP64 (hi + lo) to partial[range][pair][128][128].
 __global__ void __launch_bounds__(kGramThreads, 1) tc_gram_kernel(const __grid_constant__ PanelMaps pm,
                                                          GramGeom g, double* __restrict__ partial,
                                                          int* __restrict__ err) {
