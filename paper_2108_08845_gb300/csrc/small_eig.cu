@@ -243,13 +243,17 @@ __global__ void __launch_bounds__(LT) level_eig_kernel(LevelArgs a) {
       __syncthreads();
       if (!s_reflect) continue;  // uniform: column already reduced
       const bool live = r0 + TRR - 1 > k;  // warp has rows in the trailing block
-      // (c) p = A u
+      // (c) p = A u.  The 12 row sums of a warp are reduced across its lanes by
+      //     halving exchanges (12 -> 6 -> 3 values per lane, xor 16 and 8), then
+      //     butterflies over the remaining 8 lanes: 20 shuffles instead of 60.
+      //     Lane l ends with rows rb .. rb+2, rb = 6 bit4(l) + 3 bit3(l).
       {
-        float acc[TRR];
+        float a3[3] = {0.f, 0.f, 0.f};
         if (live) {
           float uc[TRC];
 #pragma unroll
           for (int c = 0; c < TRC; ++c) uc[c] = uvec[c0 + c];
+          float acc[TRR];
 #pragma unroll
           for (int r = 0; r < TRR; ++r) {
             float t = 0.f;
@@ -257,29 +261,46 @@ __global__ void __launch_bounds__(LT) level_eig_kernel(LevelArgs a) {
             for (int c = 0; c < TRC; ++c) t = fmaf(at[r][c], uc[c], t);
             acc[r] = t;
           }
+          const bool h16 = (lane & 16) != 0, h8 = (lane & 8) != 0;
+          float a6[6];
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-            for (int r = 0; r < TRR; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
-        } else {
-#pragma unroll
-          for (int r = 0; r < TRR; ++r) acc[r] = 0.f;
-        }
-        // lane r < TRR publishes row r (spreads the stores over the warp)
-        float up = 0.f;
-#pragma unroll
-        for (int r = 0; r < TRR; ++r)
-          if (lane == r) {
-            pvec[r0 + r] = acc[r];
-            up = acc[r] * uvec[r0 + r];
+          for (int j = 0; j < 6; ++j) {
+            const float send = h16 ? acc[j] : acc[j + 6];
+            const float keep = h16 ? acc[j + 6] : acc[j];
+            a6[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
           }
-        up = warp_sum(up);
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            const float send = h8 ? a6[j] : a6[j + 3];
+            const float keep = h8 ? a6[j + 3] : a6[j];
+            a3[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+          }
+#pragma unroll
+          for (int o = 4; o > 0; o >>= 1)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) a3[j] += __shfl_xor_sync(0xffffffffu, a3[j], o);
+        }
+        // one lane of each group of 8 publishes its three rows
+        const int rb = r0 + ((lane >> 4) & 1) * 6 + ((lane >> 3) & 1) * 3;
+        float up = 0.f;
+        if ((lane & 7) == 0) {
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            pvec[rb + j] = a3[j];
+            up = fmaf(a3[j], uvec[rb + j], up);
+          }
+        }
+        up += __shfl_xor_sync(0xffffffffu, up, 8);
+        up += __shfl_xor_sync(0xffffffffu, up, 16);
         if (lane == 0) red[warp] = up;
       }
       __syncthreads();
       // (d) rank-2 update in registers
       if (live) {
-        const float uau = warp_sum(lane < LW ? red[lane] : 0.f);
+        // u^T A u from the warps' partials: every thread sums them in the same order
+        float uau = 0.f;
+#pragma unroll
+        for (int i = 0; i < LW; ++i) uau += red[i];
         float ur[TRR], wr[TRR], ucv[TRC], wc[TRC];
 #pragma unroll
         for (int r = 0; r < TRR; ++r) {
