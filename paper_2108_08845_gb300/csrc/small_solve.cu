@@ -147,14 +147,19 @@ __global__ void copy_cols_kernel(const double* __restrict__ src, double* __restr
 }
 
 // Sort the refined eigenpairs, truncate to k1 and form the update coefficients.
+constexpr int kFinCols = 8;  // output columns per finalize block
+
 __global__ void finalize_kernel(int n, int nJ, int kc, int k1, const double* __restrict__ X,
                                 const double* __restrict__ lamJ, const double* __restrict__ D,
                                 double ff, double sig_floor, float* __restrict__ T,
                                 __nv_bfloat16* __restrict__ T3, double* __restrict__ T64,
                                 double* __restrict__ Dnew, int* __restrict__ info) {
+  // block b takes output columns [kFinCols b, kFinCols (b + 1)); the ordering and
+  // the singular values are formed by every block (a few hundred operations)
   __shared__ int order[kMaxN];
-  __shared__ double sig[kMaxN], xn[kMaxN];
+  __shared__ double sig[kMaxN], inv[kMaxN];
   const int tid = threadIdx.x;
+  const int kb0 = blockIdx.x * kFinCols, kb1 = min(k1, kb0 + kFinCols);
   if (tid < kMaxN) order[tid] = 0;
   __syncthreads();
   if (tid < nJ) {
@@ -171,12 +176,6 @@ __global__ void finalize_kernel(int n, int nJ, int kc, int k1, const double* __r
     const double l = lamJ[order[tid]];
     sig[tid] = (l > 0.0) ? sqrt(l) : 0.0;
     if (!isfinite(l)) atomicOr(&info[2], 4);
-    double x2 = 0.0;
-    for (int i = 0; i < n; ++i) {
-      const double x = X[i + (int64_t)order[tid] * n];
-      x2 = fma(x, x, x2);
-    }
-    xn[tid] = sqrt(x2);
   }
   __syncthreads();
   const double s0 = sig[0];
@@ -186,16 +185,23 @@ __global__ void finalize_kernel(int n, int nJ, int kc, int k1, const double* __r
       if (!isfinite(s) || !isfinite(s0)) atomicOr(&info[2], 4);
       else atomicOr(&info[2], 1);
       s = 0.0;
-      sig[tid] = 0.0;
     }
-    Dnew[tid] = s;
+    if (blockIdx.x == 0) Dnew[tid] = s;
+    // this block's columns: 1 / (sigma_k ||x_k||)
+    if (tid >= kb0 && tid < kb1) {
+      double x2 = 0.0;
+      for (int i = 0; i < n; ++i) {
+        const double x = X[i + (int64_t)order[tid] * n];
+        x2 = fma(x, x, x2);
+      }
+      inv[tid] = (s > 0.0) ? 1.0 / (s * sqrt(x2)) : 0.0;
+    }
   }
   __syncthreads();
-  for (int e = tid; e < n * k1; e += blockDim.x) {
-    const int i = e % n, k = e / n;
-    const double s = sig[k];
+  for (int e = tid; e < n * (kb1 - kb0); e += blockDim.x) {
+    const int i = e % n, k = kb0 + e / n;
     const double scale = (i < kc) ? ff * D[i] : 1.0;
-    const double t = (s > 0.0) ? scale * X[i + (int64_t)order[k] * n] / (s * xn[k]) : 0.0;
+    const double t = scale * X[i + (int64_t)order[k] * n] * inv[k];
     T[i + (int64_t)k * n] = (float)t;
     if (T64) T64[i + (int64_t)k * n] = t;
     if (T3) {
@@ -210,7 +216,7 @@ __global__ void finalize_kernel(int n, int nJ, int kc, int k1, const double* __r
       T3[2 * n + i + (int64_t)k * 3 * n] = lo;
     }
   }
-  if (tid == 0) info[3] = k1;
+  if (tid == 0 && blockIdx.x == 0) info[3] = k1;
 }
 
 // Upper Cholesky R^T R = G (FP64, one CTA): row i of R from rows < i.
@@ -291,8 +297,8 @@ cudaError_t small_solve_launch(const SmallWork& w, int n, int kc, int k1, const 
   if ((e = dgemm<false>(n, nJ, n, 1.0, w.H, n, w.X, n, 0.0, nullptr, n, w.W, n, st))) return e;
   rayleigh_kernel<<<nJ, 256, 0, st>>>(n, nJ, w.X, w.W, w.lamJ);
   if ((e = cudaGetLastError())) return e;
-  finalize_kernel<<<1, 256, 0, st>>>(n, nJ, kc, k1, w.X, w.lamJ, D, ff, sqrt(lambda_floor(w)), w.T,
-                                    nullptr, w.T64, w.Dnew, w.info);
+  finalize_kernel<<<(unsigned)ceil_div(k1 > 0 ? k1 : 1, kFinCols), 256, 0, st>>>(
+      n, nJ, kc, k1, w.X, w.lamJ, D, ff, sqrt(lambda_floor(w)), w.T, nullptr, w.T64, w.Dnew, w.info);
   *launches = nl + 1 + 6 * refine_steps + 3;
   return cudaGetLastError();
 }
