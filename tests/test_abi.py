@@ -36,3 +36,26 @@ def test_library_exports_every_declared_symbol():
 def test_status_strings_without_gpu():
     assert psvd.status_string(psvd.PSVD_ERR_SHAPE) == "unsupported shape"
     assert psvd.status_string(12345) == "unknown status"
+
+
+def test_new_entry_points_reject_bad_arguments_without_gpu():
+    # every check below returns before any CUDA call
+    lib = psvd.load()
+    C = ctypes
+    assert lib.psvd_update_adjoint(None, 0, None, 0, None, None, 0, 1, psvd.PSVD_F32, 1, None, 0,
+                                   None, None, 0, None, None, 0, None, None, 0) == \
+        psvd.PSVD_ERR_INVALID_ARG
+    assert lib.psvd_autotune(None, None, 0, 1, psvd.PSVD_F32, None) == psvd.PSVD_ERR_INVALID_ARG
+    cfg = psvd.psvd_config(1024, 8, 16, 1.0, psvd.PSVD_PREC_FP32, 0, 10, 0, 0, None)
+    g = C.c_void_p()
+    assert lib.psvd_group_create(None, 4, C.byref(cfg)) == psvd.PSVD_ERR_INVALID_ARG
+    assert lib.psvd_group_create(C.byref(g), 0, C.byref(cfg)) == psvd.PSVD_ERR_INVALID_ARG
+    assert g.value is None
+    assert lib.psvd_group_initialize(None, None, 1024, 16, psvd.PSVD_F32) == psvd.PSVD_ERR_INVALID_ARG
+    assert lib.psvd_group_incorporate_data(None, None, 1024, 16, psvd.PSVD_F32) == \
+        psvd.PSVD_ERR_INVALID_ARG
+    assert lib.psvd_group_member(None, 0) is None
+    assert lib.psvd_group_status(None) == psvd.PSVD_ERR_INVALID_ARG
+    assert lib.psvd_group_stats(None, None, None) == psvd.PSVD_ERR_INVALID_ARG
+    lib.psvd_group_destroy(None)  # a null group is ignored
+    assert psvd.status_string(psvd.PSVD_WARN_DEGENERATE).startswith("warning: coincident")
