@@ -10,7 +10,7 @@ update, Sec. 3.1), Algorithm 2 (APMOS, Sec. 3.2), the randomized low-rank SVD of
 Sec. 3.3, and the Philox4x32-10 Gaussian test matrix.  Inputs of any float dtype
 are widened exactly to float64 here; outputs are float64.
 
-Readings of the paper taken where it is silent (listed with reasons in the design doc):
+Readings of the paper taken where it is silent:
   * Algorithm 1 always truncates to K modes after each batch (steps 3 and 5),
   * the forget factor scales U*D (the singular values), not their squares,
   * singular values are sorted descending with a stable order for ties,

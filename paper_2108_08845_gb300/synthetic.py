@@ -6,7 +6,7 @@ FP64 oracle; parity tests generate on the CPU and hand identical bits to both.
 Everything is plain PyTorch so one recipe runs on CPU (tests) or GPU (benchmark
 inputs too large for host memory); the two devices draw different random bits.
 
-Recipes (the readings of underspecified workload parameters are listed in the design doc):
+Recipes (where the workload description leaves a parameter open, the reading taken is stated):
 
 * ``low_rank``: A = U0 diag(s) V0^T + noise, U0 (M x r) and V0 (N x r) orthonormal
   from seeded Gaussian matrices + QR, s_i = 10^(-i/8) for i = 0..r-1, i.i.d.
