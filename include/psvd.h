@@ -148,8 +148,12 @@ int psvd_parallel_qr(psvd_handle h, const void* P, int64_t ldp, int32_t n, int32
  * W = [V~^1 S~^1, ...], SVD of W (r2 kept), then U~^b_j = A^b X~_j / L~_j.
  * Outputs: U_out (Mtot x r2, FP32, ldu >= Mtot), L_out (r2, FP64, descending),
  * host or device.  N <= 192, r1 <= N, r2 <= min(N, r1*nparts).  Runs on the
- * FP32 path for either handle precision and uses the handle only for its
- * stream and staging buffer; its workspaces (one per concurrent lane: the
+ * FP32 path for either handle precision and uses the handle for its stream,
+ * staging buffer and randomization settings: with low_rank set, the SVD of W is
+ * the paper's low_rank_svd (Listing 3), a randomized SVD with l = min(r2 +
+ * oversample, N, r1*nparts) Gaussian sketch columns from Philox stream
+ * 0x41504D4F53 of the handle's seed and power_iters power steps, each local factor
+ * column signed so that its entries sum to >= 0.  Its workspaces (one per concurrent lane: the
  * blocks' local solves run on up to 16 streams of the handle's own) are kept
  * by the handle after the first call and grown when a call needs more.  The
  * launch sequence is captured into a CUDA graph on the first call with a given
