@@ -9,19 +9,25 @@ N(0, 1e-4^2) noise, generated on the GPU.  Each batch is 2 GiB, larger than the
 
 A step is one psvd_incorporate_data call: panel Gram, small eigen-solve and
 mode update.  W untimed warm-up steps follow psvd_initialize, then exactly K
-steps are timed with CUDA events on the library's stream, bracketed by a
-barrier and torch.cuda.synchronize().  Under torchrun every rank runs an
-independent replica on its own GPU (the path has no exchange step on one GPU);
-value = all ranks' snapshots / the slowest rank's time.
+steps are timed with CUDA events on the library's stream, bracketed by
+torch.cuda.synchronize().  One GPU only: the tensor-core Gram multicasts its
+shared panel slab across a thread-block cluster with TMA, which this library
+keeps to single-GPU runs, so a multi-process launch is refused.
+
+The accuracy of the headline arm is measured at the same size: a PSVD_PREC_FP64
+handle (the on-device full-precision path, itself checked against the oracle by
+the tests) runs the same batches, and the line reports the largest relative
+singular-value error and the largest principal angle of the K-mode subspace.
 
 --impl reference times the FP64 CPU oracle (the only reference implementation:
 the paper has no code of its own to install) on a bounded sample of the same
-workload on the host cores.
+workload on the host cores; --workload cpu_table times it on whole workloads.
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -113,12 +119,11 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def make_batches(device, count: int, rank: int = 0):
+def make_batches(device, count: int):
     import torch
 
-    from paper_2108_08845_gb300 import replicas, synthetic
-    gen = synthetic.TravellingWaves(NY, NX, NMODES, DECAY, NOISE, replicas.stream_seed(SEED, rank),
-                                    corr_len=CORR,
+    from paper_2108_08845_gb300 import synthetic
+    gen = synthetic.TravellingWaves(NY, NX, NMODES, DECAY, NOISE, SEED, corr_len=CORR,
                                     device=device, dtype=torch.float32)
     out = []
     for i in range(count):
@@ -140,8 +145,6 @@ def run_arm(psvd, batches, precision, steps, warmup, stream, sampler=None):
             psvd.psvd_incorporate_data(h, batches[1 + i % (nb - 1)])
         psvd.psvd_set_profiling(h, True)
         torch.cuda.synchronize()
-        if torch.distributed.is_initialized():
-            torch.distributed.barrier()
         if sampler:
             sampler.start()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -230,44 +233,74 @@ def roofline(res, precision, hbm_peak, peak_kind):
             "dominant_phase": phases[dom]}, avg
 
 
-def cpu_sample(updates: int = 2, ny: int = 128, nx: int = 256):
-    """Oracle on a bounded sample: a ny x nx grid of the same recipe, K = 64, B = 128,
-    initialise + `updates` updates; per-update time scaled by M_full / M_sample
-    (the oracle's work per update is linear in M)."""
+# Bounded CPU sample of the headline workload: one update (after its own
+# initialisation) on each of two grids of the same recipe, 128 x 512 and 256 x 512.
+# The oracle's update time is t(M) = a + b M: Householder QR and Q U~ are linear in
+# the rows, the Jacobi SVD of the (K+B)^2 factor is not; the two timings fix a and
+# b, and t(M_full) is the per-update time at the headline size.
+CPU_SAMPLE_GRIDS = ((128, 512), (256, 512))
+
+
+def _oracle_batches(ny, nx, count, seed=SEED):
+    """`count` batches of the headline recipe on an ny x nx grid, BF16 values widened
+    to FP64 (what the oracle receives), generated with torch on the host."""
     import torch
 
-    import oracle
     from paper_2108_08845_gb300 import synthetic
-    gen = synthetic.TravellingWaves(ny, nx, NMODES, DECAY, NOISE, SEED, corr_len=CORR)
-    bs = [gen.batch(i, BATCH).to(torch.bfloat16).double().numpy() for i in range(updates + 1)]
-    U, D = oracle.stream_initialize(bs[0], K_MODES)
-    t0 = time.perf_counter()
-    for b in bs[1:]:
-        U, D = oracle.stream_update(U, D, b, FF, K_MODES)
-    dt = (time.perf_counter() - t0) / updates
-    m = ny * nx
-    scaled = dt * (M_FULL / m)
-    return {"value": BATCH / scaled, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-            "sample": f"{updates} updates at M={m} ({ny}x{nx} grid), K=64, B=128, "
-                      f"{dt:.2f} s per update, scaled by M_full/M_sample={M_FULL // m}"}
+    gen = synthetic.TravellingWaves(ny, nx, NMODES, DECAY, NOISE, seed, corr_len=CORR)
+    return [gen.batch(i, BATCH).to(torch.bfloat16).double().numpy() for i in range(count)]
+
+
+class CpuSample:
+    """The oracle timed on the bounded sample above (data generated once)."""
+
+    def __init__(self):
+        import oracle
+        self.oracle = oracle
+        self.data = []
+        for ny, nx in CPU_SAMPLE_GRIDS:
+            bs = _oracle_batches(ny, nx, 2)
+            U, D = oracle.stream_initialize(bs[0], K_MODES)
+            self.data.append((ny * nx, U, D, bs[1]))
+
+    def run(self):
+        ts = []
+        for m, U, D, A in self.data:
+            t0 = time.perf_counter()
+            self.oracle.stream_update(U, D, A, FF, K_MODES)
+            ts.append(time.perf_counter() - t0)
+        (m1, _, _, _), (m2, _, _, _) = self.data
+        b = (ts[1] - ts[0]) / (m2 - m1)
+        a = ts[0] - b * m1
+        t_full = a + b * M_FULL
+        return {"value": BATCH / t_full, "unit": UNIT, "cores": self.oracle.threads(),
+                "kind": "oracle",
+                "sample": (f"one update (K=64, B=128, ff=0.95) of the same recipe on grids "
+                           f"{CPU_SAMPLE_GRIDS[0][0]}x{CPU_SAMPLE_GRIDS[0][1]} and "
+                           f"{CPU_SAMPLE_GRIDS[1][0]}x{CPU_SAMPLE_GRIDS[1][1]} "
+                           f"({ts[0]:.2f} s and {ts[1]:.2f} s); per-update time at M={M_FULL} "
+                           f"from the fit t(M) = a + b M through both: {t_full:.1f} s")}
+
+
+def cpu_sample():
+    return CpuSample().run()
 
 
 def reference_main(args):
-    from paper_2108_08845_gb300 import replicas
-    ws, rank, _ = replicas.world()
+    rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    samples = []
+    sample = CpuSample()
     for _ in range(args.warmup):
-        cpu_sample(1, 64, 128)
+        sample.run()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        samples.append(cpu_sample(1, 64, 128))
+    runs = [sample.run() for _ in range(args.steps)]
     wall = time.perf_counter() - t0
-    v = statistics.median(s["value"] for s in samples)
-    cb = dict(samples[0])
+    v = statistics.median(r["value"] for r in runs)
+    cb = dict(runs[0])
     cb["value"] = v
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+            "n_gpus": int(os.environ.get("WORLD_SIZE", args.gpus)),
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": BATCH / v * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "M": M_FULL, "K": K_MODES,
@@ -276,6 +309,56 @@ def reference_main(args):
                                         "d2h_bytes_per_step": 0},
             "wall_s": wall}
     print(json.dumps(line))
+    return 0
+
+
+def cpu_table_main(args):
+    """The oracle on whole workloads, with one thread and with every host thread:
+    the low-rank workload (M = 4096, K = 10, 4 batches of B = 25, ff = 1) and the
+    plain method at scale (M = 2^20, K = 32, 16 batches of B = 64, ff = 0.95,
+    randomized range finder p = 10, q = 1) in full, and the headline workload
+    (M = 2^23, K = 64, B = 128) on two whole updates after its initialisation.
+    Snapshot generation is not timed.  Prints one JSON line per measurement."""
+    import torch
+
+    import oracle
+    from paper_2108_08845_gb300 import synthetic
+    all_threads = oracle.threads()
+
+    def emit(name, threads, snaps, secs, extra=None):
+        d = {"workload": name, "threads": threads, "snapshots": snaps, "seconds": secs,
+             "snapshots_per_s": snaps / secs}
+        d.update(extra or {})
+        print(json.dumps(d), flush=True)
+
+    A, _, _, _ = synthetic.low_rank(4096, 100, 40, 1e-8, seed=1234)
+    c1 = [A[:, i:i + 25].float().double().numpy() for i in range(0, 100, 25)]
+    gen = synthetic.TravellingWaves(1024, 1024, 64, 1.5, 1e-3, seed=1235, corr_len=16.0)
+    c2 = [gen.batch(i, 64).float().double().numpy() for i in range(16)]
+    for threads in (1, all_threads):
+        oracle.set_threads(threads)
+        t0 = time.perf_counter()
+        oracle.stream_run(c1, 10, 1.0)
+        emit("M=4096, K=10, 4 batches of B=25, ff=1 (init + 3 updates)", threads, 100,
+             time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        oracle.rsvd_run(c2, 32, 0.95, 10, 1, 42)
+        emit("M=2^20, K=32, 16 batches of B=64, ff=0.95, p=10, q=1 (init + 15 updates)",
+             threads, 1024, time.perf_counter() - t0)
+    oracle.set_threads(all_threads)
+    gen = synthetic.TravellingWaves(NY, NX, NMODES, DECAY, NOISE, SEED, corr_len=CORR,
+                                    device="cuda" if torch.cuda.is_available() else "cpu")
+    U = D = None
+    for i in range(3):
+        b = gen.batch(i, BATCH).to(torch.bfloat16).double().cpu().numpy()
+        t0 = time.perf_counter()
+        if i == 0:
+            U, D = oracle.stream_initialize(b, K_MODES)
+            continue
+        U, D = oracle.stream_update(U, D, b, FF, K_MODES)
+        emit(f"M=2^23, K=64, B=128, ff=0.95: update {i}", all_threads, BATCH,
+             time.perf_counter() - t0, {"fit_prediction_s": BATCH / CpuSample().run()["value"]}
+             if i == 2 else None)
     return 0
 
 
@@ -397,6 +480,57 @@ def streams_main(args):
     return 0
 
 
+def accuracy_leg(psvd, batches, stream, updates=7):
+    """Singular values and modes of the tensor-core arm against a PSVD_PREC_FP64 handle
+    on the same batches (initialisation + `updates` updates) at the benchmark's size.
+    Returns the largest relative singular-value error and the largest principal angle
+    between the two K-mode subspaces (computed in FP64 on the device)."""
+    import torch
+
+    nb = len(batches)
+    out = {}
+    for name, prec in (("bf16_tc", psvd.PSVD_PREC_BF16_TC), ("fp64", psvd.PSVD_PREC_FP64)):
+        h = psvd.psvd_create(M_FULL, K_MODES, BATCH, FF, prec, stream=stream)
+        try:
+            psvd.psvd_initialize(h, batches[0])
+            for i in range(updates):
+                psvd.psvd_incorporate_data(h, batches[1 + i % (nb - 1)])
+            k = psvd.psvd_num_modes(h)
+            s = torch.empty(k, dtype=torch.float64, device="cuda")
+            psvd.psvd_get_singular_values(h, s)
+            if prec == psvd.PSVD_PREC_FP64:
+                U = torch.empty((k, M_FULL), dtype=torch.float64, device="cuda").T
+                psvd.psvd_get_modes_f64(h, U)
+            else:
+                U32 = torch.empty((k, M_FULL), dtype=torch.float32, device="cuda").T
+                psvd.psvd_get_modes(h, U32)
+                U = U32.double()
+                del U32
+        finally:
+            psvd.psvd_destroy(h)
+        out[name] = (s, U)
+    (s1, U1), (s2, U2) = out["bf16_tc"], out["fp64"]
+    sig = ((s1 - s2).abs() / s2).max().item()
+
+    def orth(U):  # Cholesky QR in FP64 (the modes are orthonormal to ~1e-5)
+        L = torch.linalg.cholesky(U.T @ U)
+        return torch.linalg.solve_triangular(L, U.T, upper=False).T
+
+    Q1 = orth(U1)
+    Q2 = orth(U2)
+    del U1, U2
+    R = Q2 - Q1 @ (Q1.T @ Q2)
+    sin_max = torch.linalg.eigvalsh(R.T @ R).max().clamp(min=0).sqrt().item()
+    del Q1, Q2, R
+    torch.cuda.empty_cache()
+    ang = math.asin(min(1.0, sin_max))
+    return {"against": "PSVD_PREC_FP64 handle on the same batches (on the device)",
+            "updates": updates, "sigma_rel_err_max": sig, "subspace_angle_rad": ang,
+            "sigma_K_over_sigma_1": (s2[-1] / s2[0]).item(),
+            "targets": {"sigma_rel_err": 1e-4, "subspace_angle_rad": 1e-3},
+            "meets_targets": bool(sig <= 1e-4 and ang <= 1e-3)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -405,18 +539,30 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="both", choices=["both", "fp32", "bf16_tc"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--ny", type=int, default=NY, help="grid rows (profiling on smaller grids)")
     ap.add_argument("--nx", type=int, default=NX, help="grid columns")
-    ap.add_argument("--workload", default="stream", choices=["stream", "apmos", "streams"],
+    ap.add_argument("--workload", default="stream",
+                    choices=["stream", "apmos", "streams", "cpu_table"],
                     help="stream: the streaming update (headline); apmos: Algorithm 2 batching; "
-                         "streams: 32 independent streams per captured graph")
+                         "streams: 32 independent streams per captured graph; cpu_table: the "
+                         "oracle on whole workloads (1 thread and all threads)")
     args = ap.parse_args()
     set_grid(args.ny, args.nx)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return reference_main(args)
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1 or args.gpus != 1:
+        print(json.dumps({"error": "one GPU only: the tensor-core Gram multicasts panel slabs "
+                                   "within a thread-block cluster, kept to single-GPU runs; "
+                                   "run with --gpus 1 and no launcher",
+                          "n_gpus": max(ws, args.gpus)}))
+        return 2
+    if args.workload == "cpu_table":
+        return cpu_table_main(args)
     if args.workload == "apmos":
         return apmos_main(args)
     if args.workload == "streams":
@@ -425,64 +571,50 @@ def main():
     import torch
 
     from paper_2108_08845_gb300 import psvd
-    from paper_2108_08845_gb300 import replicas
-    ws, rank, local = replicas.world()
-    torch.cuda.set_device(local)
-    if ws > 1:
-        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     hbm_peak, bf16_peak, peak_kind = _peaks()
 
     arms = {"both": ["bf16_tc", "fp32"], "fp32": ["fp32"], "bf16_tc": ["bf16_tc"]}[args.precision]
     prec_code = {"fp32": psvd.PSVD_PREC_FP32, "bf16_tc": psvd.PSVD_PREC_BF16_TC}
     nb = min(32, 1 + args.warmup + args.steps)
-    batches = make_batches("cuda", nb, rank)
+    batches = make_batches("cuda", nb)
     results = {}
     for arm in arms:
-        sampler = ClockSampler(local) if rank == 0 else None
-        try:
-            results[arm] = run_arm(psvd, batches, prec_code[arm], args.steps, args.warmup, stream,
-                                   sampler)
-        except psvd.PsvdError as e:
-            if e.status != psvd.PSVD_ERR_UNSUPPORTED or args.precision != "both":
-                raise
-            results[arm] = None  # the tensor-core path is not available in this build
-    head = next(a for a in arms if results.get(a))
+        results[arm] = run_arm(psvd, batches, prec_code[arm], args.steps, args.warmup, stream,
+                               ClockSampler(0))
+    head = arms[0]
     r = results[head]
     e2e = (run_e2e(psvd, batches, prec_code[head], args.e2e_steps, stream) if args.e2e_steps > 0
            else None)
-    ms_max, e2e_min = replicas.reduce_timing(r["ms"], e2e["value"] if e2e else None, ws,
-                                             device="cuda")
-    value = replicas.job_throughput(ws, args.steps, BATCH, ms_max)
-    if e2e:
-        e2e["value"] = e2e_min * ws
-    if rank == 0:
-        rf, avg = roofline(r, head, hbm_peak, peak_kind)
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "bf16" if head == "bf16_tc" else "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "M": M_FULL, "K": K_MODES, "B": BATCH, "ff": FF,
-                           "precision": head, "replicas": ws,
-                           "l2": "inputs larger than L2 (2 GiB per batch), no flush"},
-                "roofline": rf, "clocks": r["clocks"], "e2e": e2e,
-                "gpu_launches": r["launches"],
-                "phase_ms_per_step": {"gram": avg[0], "small_solve": avg[1], "update": avg[2]},
-                "status": r["status"]}
-        for arm in arms:
-            if arm != head and results.get(arm):
-                ra = results[arm]
-                line[f"{arm}_arm"] = {"value": ws * args.steps * BATCH / (ra["ms"] * 1e-3),
-                                      "ms_per_step": ra["ms"] / args.steps,
-                                      "phase_ms_per_step": [ra["prof_ms"][i] / max(1, ra["prof_cnt"][i])
-                                                            for i in range(3)]}
-            elif arm != head:
-                line[f"{arm}_arm"] = None
-        if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_sample()
-        print(json.dumps(line))
-    if ws > 1:
-        torch.distributed.destroy_process_group()
+    ms = r["ms"]
+    value = args.steps * BATCH / (ms * 1e-3)
+    rf, avg = roofline(r, head, hbm_peak, peak_kind)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16" if head == "bf16_tc" else "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "M": M_FULL, "K": K_MODES, "B": BATCH, "ff": FF,
+                       "precision": head,
+                       "l2": "inputs larger than L2 (2 GiB per batch), no flush"},
+            "roofline": rf, "clocks": r["clocks"], "e2e": e2e,
+            "gpu_launches": r["launches"],
+            "phase_ms_per_step": {"gram": avg[0], "small_solve": avg[1], "update": avg[2]},
+            "status": r["status"]}
+    for arm in arms[1:]:
+        ra = results[arm]
+        line[f"{arm}_arm"] = {"value": args.steps * BATCH / (ra["ms"] * 1e-3),
+                              "ms_per_step": ra["ms"] / args.steps,
+                              "phase_ms_per_step": [ra["prof_ms"][i] / max(1, ra["prof_cnt"][i])
+                                                    for i in range(3)],
+                              "clocks": ra["clocks"]}
+    if head == "bf16_tc" and not args.no_accuracy:
+        line["accuracy"] = accuracy_leg(psvd, batches, stream)
+    del batches
+    torch.cuda.empty_cache()
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_sample()
+    print(json.dumps(line))
     return 0
 
 

@@ -44,8 +44,13 @@ extern "C" {
 #define PSVD_OK 0
 #define PSVD_WARN_RANK_DEFICIENT 1   /* a kept singular value is (numerically) zero;
                                         its mode is set to zero (Alg. 2, Lambda_j = 0) */
-#define PSVD_WARN_NOT_CONVERGED 2    /* the small Jacobi eigen-solve hit its sweep cap;
-                                        results are those of the last sweep */
+#define PSVD_WARN_NOT_CONVERGED 2    /* the small eigen-solve used all of its scale levels
+                                        (4; 6 on a PSVD_PREC_FP64 handle) before it had
+                                        resolved the K + 8 leading eigenpairs of the
+                                        scaled Gram down to the Gram's resolution floor
+                                        (1e-9 of the largest eigenvalue; 1e-13 for FP64);
+                                        the unresolved kept pairs carry only the FP32
+                                        accuracy of the last level */
 #define PSVD_WARN_DEGENERATE 3       /* psvd_update_adjoint: two kept singular values, or
                                         the last kept and the first dropped one, coincide
                                         (to 1e-13 relative in s^2); the derivative is
@@ -170,9 +175,10 @@ int psvd_parallel_svd(psvd_handle h, const void* A, int64_t lda, const int64_t* 
  * a process whose device memory is reserved by another allocator, or a
  * latency-critical loop where cudaMalloc's implicit device synchronisation
  * would stall other streams).  No handle is needed.
- *   P      device pointer to the panel, M x n column-major, ldp >= M, dtype
- *          PSVD_F32 or PSVD_BF16 (host pointers are rejected: there is no
- *          staging buffer to copy them into)
+ *   P      pointer to the panel in the current device's memory (or managed
+ *          memory), M x n column-major, ldp >= M, dtype PSVD_F32 or PSVD_BF16;
+ *          host pointers (no staging buffer to copy them into) and pointers to
+ *          another GPU's memory are rejected with PSVD_ERR_INVALID_ARG
  *   R_out  n x n FP64, leading dimension n, upper triangular with diag >= 0
  *          (host or device); stream: cudaStream_t, NULL = default stream
  * Limits: n <= 128 and M >= n, else PSVD_ERR_SHAPE.  Scratch: a 3.4 MB

@@ -344,5 +344,25 @@ def gaussian_matrix(seed: int, stream: int, rows: int, cols: int) -> np.ndarray:
     return g.reshape((cols, rows)).T.copy(order="F")
 
 
+def _omp(name):
+    try:
+        return getattr(_load(), name)
+    except AttributeError:  # built without OpenMP: one thread
+        return None
+
+
 def threads() -> int:
-    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    """Threads the oracle's parallel loops use (1 when built without OpenMP)."""
+    f = _omp("omp_get_max_threads")
+    if f is None:
+        return 1
+    f.restype = C.c_int
+    return int(f())
+
+
+def set_threads(n: int) -> None:
+    """Thread count of the oracle's parallel loops (results do not depend on it)."""
+    f = _omp("omp_set_num_threads")
+    if f is not None:
+        f.argtypes = [C.c_int]
+        f(int(n))

@@ -2,8 +2,9 @@
 // launch sequence of the per-batch update of Algorithm 1 (Sec. 3.1):
 //
 //   Gram of [U | A] over row chunks  ->  FP64 reduction + diag(ff D, 1) scaling
-//   ->  eigen-decomposition of the small (K+B)^2 matrix (FP32 Jacobi + FP64
-//   refinement)  ->  T = S V diag(1/sigma)  ->  U_new = [U | A] T.
+//   ->  eigen-decomposition of the small (K+B)^2 matrix (FP32 tridiagonal
+//   solves on scale levels + FP64 refinement)  ->  T = S V diag(1/sigma)
+//   ->  U_new = [U | A] T.
 //
 // All device work is enqueued on the handle's stream; nothing runs on the host
 // but argument checks, pointer classification and launch configuration.
@@ -334,7 +335,8 @@ const char* psvd_status_string(int s) {
   switch (s) {
     case PSVD_OK: return "ok";
     case PSVD_WARN_RANK_DEFICIENT: return "warning: a kept singular value is numerically zero";
-    case PSVD_WARN_NOT_CONVERGED: return "warning: Jacobi eigen-solve reached its sweep limit";
+    case PSVD_WARN_NOT_CONVERGED:
+      return "warning: the eigen-solve used all its scale levels before resolving every kept pair";
     case PSVD_WARN_DEGENERATE:
       return "warning: coincident singular values at a kept index; the derivative is undefined";
     case PSVD_ERR_INVALID_ARG: return "invalid argument";

@@ -52,13 +52,23 @@ int scratch_for_current_device(double** out) {
   return PSVD_OK;
 }
 
-bool is_device_pointer(const void* p) {
+// True for managed memory and for device memory of the current device (the
+// kernels run there; a panel on another GPU is rejected rather than read across
+// the interconnect or faulted on).
+bool is_current_device_pointer(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  if (a.type != cudaMemoryTypeDevice) return false;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.device == dev;
 }
 
 }  // namespace
@@ -68,7 +78,8 @@ extern "C" int psvd_parallel_qr_static(const void* P, int64_t ldp, int64_t M, in
   if (!P || !R_out || M < 1 || n < 1 || ldp < M) return PSVD_ERR_INVALID_ARG;
   if (dtype != PSVD_F32 && dtype != PSVD_BF16) return PSVD_ERR_INVALID_ARG;
   if (n > kStaticMaxN || M < n) return PSVD_ERR_SHAPE;
-  if (!is_device_pointer(P)) return PSVD_ERR_INVALID_ARG;  // no staging buffer to copy into
+  // host panels: no staging buffer to copy them into; other GPUs: see above
+  if (!is_current_device_pointer(P)) return PSVD_ERR_INVALID_ARG;
   double* scratch = nullptr;
   if (int rc = scratch_for_current_device(&scratch)) return rc;
   double* partial = scratch;

@@ -2,8 +2,8 @@
 
 Row blocks of uneven sizes stand in for the paper's ranks.  Tolerances are the
 FP32 ones of the streaming path (see test_gpu_fp32): 1e-5 relative on the
-singular values and 1e-4 rad on the leading subspace, widened by the FP32
-representation floor u32 * sigma_1 / sigma_i.
+singular values and 1e-4 rad on the leading subspace, flat, widened by the FP32
+representation floor u32 * sigma_1 / sigma_i only for sigma_i below 1e-2 sigma_1.
 """
 import numpy as np
 import pytest
@@ -43,7 +43,9 @@ def _gpu_apmos(A, offsets, r1, r2, device="cuda"):
 
 
 def _compare(U, L, Uo, Lo, k=None):
-    tol = 1e-5 + 8 * U32 * Lo[0] / Lo
+    # flat bars; the FP32 representation floor only where sigma_i (or the gap) is
+    # below 1e-2 sigma_1
+    tol = 1e-5 + np.where(Lo < 1e-2 * Lo[0], 8 * U32 * Lo[0] / Lo, 0.0)
     e = np.abs(L - Lo) / Lo
     assert np.all(e <= tol), f"L rel err {e.max():.3e}"
     k = k or len(Lo)
@@ -52,7 +54,8 @@ def _compare(U, L, Uo, Lo, k=None):
     Uon = Uo[:, :k] / np.linalg.norm(Uo[:, :k], axis=0)
     gap = Lo[k - 1] - Lo[k] if k < len(Lo) else Lo[k - 1]
     ang = max_principal_angle(Un, Uon)
-    assert ang <= 1e-4 + 8 * U32 * Lo[0] / gap, f"subspace angle {ang:.3e}"
+    atol = 1e-4 + (8 * U32 * Lo[0] / gap if gap < 1e-2 * Lo[0] else 0.0)
+    assert ang <= atol, f"subspace angle {ang:.3e} > {atol:.3e}"
     return e.max(), ang
 
 

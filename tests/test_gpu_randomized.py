@@ -67,19 +67,26 @@ def test_randomized_shapes(M, K, B, nb, ff, p, q):
 
 
 def test_randomized_sketch_wider_than_rank():
-    # exact rank 12 < l = 26: the range finder drops the null directions
+    # exact rank 12 < l = 26: the range finder keeps the 12 directions of the data and
+    # leaves the rest at the Gram's resolution.  The oracle (FP64 Householder on the
+    # panel) puts sigma_13.. at the rounding level of the FP32 data; the library reports
+    # every singular value below its resolution 2 sqrt(n * 1e-9) sigma_1 (n = K + B = 48)
+    # as zero with PSVD_WARN_RANK_DEFICIENT, so the two agree to that resolution.
     A, _, _, _ = synthetic.low_rank(4000, 96, 12, 0.0, seed=3,
                                     s=[0.7 ** i for i in range(12)])
     bs = _f32(_batches(A, 32))
     U, D, codes = _gpu_rsvd(bs, 16, 0.95, 10, 1, seed=1)
     assert all(c in (psvd.PSVD_OK, psvd.PSVD_WARN_RANK_DEFICIENT) for c in codes)
     Uo, Do = _oracle_rsvd(bs, 16, 0.95, 10, 1, seed=1)
-    assert np.all(D[12:] <= 1e-4 * D[0])
+    res = 2.0 * np.sqrt(48 * 1e-9) * Do[0]
+    assert np.all(Do[12:] <= res)          # the oracle's tail is below the resolution too
+    assert np.all(D[12:] == 0) and np.all(U[:, 12:] == 0)
+    assert np.all(np.abs(D[12:] - Do[12:]) <= res)
     e = np.abs(D[:12] - Do[:12]) / Do[:12]
-    assert e.max() <= 1e-5 + 8 * U32 * Do[0] / Do[11], f"sigma rel err {e.max():.3e}"
+    assert e.max() <= 1e-5, f"sigma rel err {e.max():.3e}"
     from tests.helpers import max_principal_angle
     ang = max_principal_angle(U[:, :12], Uo[:, :12])
-    assert ang <= 1e-4 + 8 * U32 * Do[0] / Do[11], f"subspace angle {ang:.3e}"
+    assert ang <= 1e-4, f"subspace angle {ang:.3e}"
 
 
 def test_randomized_full_sketch_equals_exact_path():
