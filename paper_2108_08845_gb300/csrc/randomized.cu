@@ -260,16 +260,9 @@ cudaError_t randomized_solve_launch(const RandWork& r, const SmallWork& w, int n
   RCK(dgemm_launch(false, n, l, n, 1.0, w.H, n, B0, n, 0.0, nullptr, n, B2, n, st));
   RCK(dgemm_launch(true, l, l, n, 1.0, B2, n, B2, n, 0.0, nullptr, l, r.Bb, l, st));
   nl += 2;
-  // B B^T = U~ Sigma^2 U~^T: the eigen-solve returns T_small = U~_K diag(1/sigma), Dnew.
-  // Resolution: a sketch direction outside the range of P keeps the Gram's noise
-  // (lambda_floor of lambda_max per coordinate, summed over the n coordinates the
-  // Gaussian column mixes) as its H-metric norm, and normalising it leaves a
-  // singular value near sqrt(n lambda_floor) sigma_1.  Singular values below twice
-  // that are not resolved by a Gram-based range finder: like the exact path's
-  // unresolved eigenvalues, their modes are set to zero (PSVD_WARN_RANK_DEFICIENT).
+  // B B^T = U~ Sigma^2 U~^T: the eigen-solve returns T_small = U~_K diag(1/sigma), Dnew
   SmallWork wb = w;
   wb.H = r.Bb;
-  wb.lam_floor = 4.0 * n * lambda_floor(w);
   int ns = 0;
   RCK(small_solve_launch(wb, l, 0, k1, nullptr, 1.0, /*refine_steps=*/3, kMaxLevels, st,
                          &ns));

@@ -4,13 +4,16 @@ Tolerances for the FP32 path: singular values within 1e-5 relative and the kept
 mode subspace within 1e-4 rad (largest principal angle), on the same seeded
 inputs (float32 bits widened exactly to float64 for the oracle).
 
-The singular-value bar is flat for every mode with sigma_i >= 1e-2 sigma_1.  Below
-that, FP32-stored modes carry a representation floor that any FP32 method has:
-they perturb the panel by ~u32 sigma_1, which moves sigma_i by a relative
-~u32 sigma_1 / sigma_i, so those modes (and only those) get 8 u32 sigma_1 / sigma_i
-added.  The subspace bar is flat, over the full K-mode subspace whenever the
-oracle's last panel separates sigma_K from sigma_K+1 by 1 % (else over the largest
-leading k that is separated that well).
+The bars are flat for every mode with sigma_i >= 1e-2 sigma_1.  Below that two
+floors of the method are added to the singular-value bar, each derived, not
+fitted: FP32-stored modes perturb the panel by ~u32 sigma_1, which moves sigma_i
+by a relative ~u32 sigma_1 / sigma_i (8 u32 sigma_1 / sigma_i); and a Gram-based
+factorisation resolves eigenvalues of the Gram to ~1e-9 lambda_1 (the library's
+stated resolution), which moves sigma_i by a relative 1e-9 sigma_1^2 / (2 sigma_i^2)
+(taken 4x).  The subspace bar is flat, over the largest leading k <= K (k = K
+when the oracle's last panel gives sigma_K+1) that the oracle separates from the
+rest by a relative gap of 1 % and whose eigenvalue gap lambda_k - lambda_k+1
+resolves that bar at the Gram's resolution (4e-9 lambda_1 / gap <= the bar).
 """
 import numpy as np
 import pytest
@@ -26,8 +29,9 @@ SIG_TOL = 1e-5
 ANG_TOL = 1e-4
 U32 = 2.0 ** -24
 U64 = 2.0 ** -53
-REL_GAP = 1e-2   # a leading subspace is compared when sigma_k - sigma_k+1 >= REL_GAP sigma_k
-FLOOR_BELOW = 1e-2  # the FP32 representation floor applies to sigma_i < FLOOR_BELOW sigma_1
+REL_GAP = 1e-2      # a leading subspace is compared when sigma_k - sigma_k+1 >= REL_GAP sigma_k
+FLOOR_BELOW = 1e-2  # the method's floors apply to sigma_i < FLOOR_BELOW sigma_1
+GRAM_RES = 1e-9     # resolution of the FP32 and tensor-core Grams, relative to lambda_1
 
 
 def _batches(A, B):
@@ -69,29 +73,37 @@ def _oracle_run_gap(batches, K, ff):
     return U, D, (float(s_all[k]) if len(s_all) > k else 0.0)
 
 
-def subspace_dim(Do, s_next=None, rel_gap=REL_GAP):
+def subspace_dim(Do, s_next=None, ang_tol=ANG_TOL, gram_res=GRAM_RES, rel_gap=REL_GAP):
     """Largest k <= K whose leading-k subspace is separated from the rest by a
-    relative gap: sigma_k - sigma_k+1 >= rel_gap sigma_k, with sigma_K+1 = s_next
-    (None: unknown, so k = K is not taken)."""
+    relative gap (sigma_k - sigma_k+1 >= rel_gap sigma_k) that the Gram's resolution
+    resolves at the angle bar (4 gram_res sigma_1^2 / (sigma_k^2 - sigma_k+1^2) <=
+    ang_tol); sigma_K+1 = s_next (None: unknown, so k = K is not taken)."""
     s = list(Do) + ([s_next] if s_next is not None else [])
     for k in range(len(Do), 0, -1):
-        if k < len(s) and s[k - 1] - s[k] >= rel_gap * s[k - 1]:
+        if k >= len(s):
+            continue
+        gap, lgap = s[k - 1] - s[k], s[k - 1] ** 2 - s[k] ** 2
+        if gap >= rel_gap * s[k - 1] and 4.0 * gram_res * s[0] ** 2 <= ang_tol * lgap:
             return k
     return 1
 
 
-def _compare(U, D, Uo, Do, sig_tol=SIG_TOL, ang_tol=ANG_TOL, unit=U32, floor=8.0, s_next=None):
-    """unit: rounding unit of the stored modes (u32 FP32, 2^-17 BF16 hi/lo pair, u64 FP64).
-    The singular-value representation floor below FLOOR_BELOW sigma_1 applies to FP32
-    and FP64 storage only; the BF16 hi/lo path is held to the flat bar."""
+def _compare(U, D, Uo, Do, sig_tol=SIG_TOL, ang_tol=ANG_TOL, unit=U32, floor=8.0, s_next=None,
+             gram_res=None):
+    """unit: rounding unit of the stored modes (u32 FP32, 2^-17 BF16 hi/lo pair, u64 FP64);
+    the storage floor applies to FP32 and FP64 storage.  gram_res: the Gram's resolution
+    relative to lambda_1 (1e-9 for the FP32 and tensor-core Grams, 1e-13 for FP64)."""
     assert U.shape == Uo.shape and D.shape == Do.shape
+    if gram_res is None:
+        gram_res = 1e-13 if unit == U64 else GRAM_RES
     tol = np.full(len(Do), sig_tol)
+    low = Do < FLOOR_BELOW * Do[0]
+    tol[low] += 4.0 * gram_res * Do[0] ** 2 / (2.0 * Do[low] ** 2)
     if unit in (U32, U64):
-        low = Do < FLOOR_BELOW * Do[0]
         tol[low] += floor * unit * Do[0] / Do[low]
     e = rel_err(D, Do)
     assert np.all(e <= tol), f"sigma rel err {e.max():.3e} (worst ratio {np.max(e / tol):.2f})"
-    k = subspace_dim(Do, s_next)
+    k = subspace_dim(Do, s_next, ang_tol, gram_res)
     e_ang = max_principal_angle(U[:, :k], Uo[:, :k])
     assert e_ang <= ang_tol, f"subspace angle {e_ang:.3e} > {ang_tol:.3e} (k={k} of {len(Do)})"
     # U_new = P V / sigma in finite precision: column i is orthonormal to ~u*sigma_1/sigma_i
