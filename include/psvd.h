@@ -313,6 +313,19 @@ int psvd_set_profiling(psvd_handle h, int32_t enable);
  * profiling was enabled (*launches_out).  Any output pointer may be NULL. */
 int psvd_get_profile(psvd_handle h, double* ms_out, int64_t* count_out, int64_t* launches_out);
 
+/* psvd_debug_set_wait_budget: testing hook of the device-side failure detection
+ * (no counterpart in the paper).  Every wait of the tensor-core kernels on a copy or
+ * on the tensor cores is bounded (about 2 s); when a budget runs out the kernel
+ * stops issuing work, waits with the full budget for the copies and matrix
+ * products it has already issued, frees its tensor memory and returns, and the
+ * handle reports PSVD_ERR_TIMEOUT.  This call sets the budget, in SM clock cycles,
+ * of the pipeline waits of the tensor-core mode-update kernel (kernel = 1) for the
+ * launches that follow, process-wide; cycles = 0 restores the default.  A budget
+ * shorter than any copy's latency makes the next update time out without a fault,
+ * which is how the tests exercise that path.  Returns PSVD_ERR_INVALID_ARG for
+ * another kernel or a negative budget.  Not synchronised with concurrent updates. */
+int psvd_debug_set_wait_budget(int32_t kernel, int64_t cycles);
+
 /* psvd_status_string: static description of a status code. */
 const char* psvd_status_string(int status);
 

@@ -8,11 +8,13 @@
 //     eigenvectors are the left singular vectors X~ of W and whose eigenvalues
 //     are L~^2;
 //   U~ = A X~ diag(1/L~) over all rows at once (the same T = X~ diag(1/L~)).
-// The local solves are latency-bound chains (the eigen-solve's level kernel runs
-// on one SM), so the blocks run concurrently: up to kLanes streams, each with its
-// own workspace, take the blocks round-robin; every block writes its factors to
-// its own slot, and W W^T sums the slots in block order after the join, so the
-// result does not depend on which lane finished first.
+// Every phase covers all blocks in one launch: the local Grams are one launch over
+// a work list of row chunks of every block (uneven blocks get proportionally many
+// chunks), their reductions one launch with a grid dimension per block, and each
+// kernel of the local eigen-solves one launch in which block b's problem is a CTA
+// (or a grid plane) of its own, so the blocks' latency-bound solves run side by side
+// on separate SMs.  Every block writes its factors to its own slot, and W W^T sums
+// the slots in block order, so the result does not depend on scheduling.
 #include <stdint.h>
 
 #include <algorithm>
@@ -24,7 +26,9 @@
 namespace psvd {
 namespace {
 
-constexpr int kLanes = 16;
+// Blocks whose local eigen-solves share one batch of launches (bounds the batch
+// workspace: 7 n x n FP64 matrices per block).
+constexpr int kMaxBatch = 128;
 
 // WW = sum_b Vs_b Vs_b^T, blocks in order, with Vs_b = T64_b[:, 0:r1] diag(sigma_b^2)
 // (T64_b: N x r1 FP64 at T64 + b * N * r1, sigma_b at sigma + b * r1).
@@ -67,17 +71,11 @@ __global__ void to_f32_kernel(const double* __restrict__ x, int64_t count, float
   if (e < count) y[e] = (float)x[e];
 }
 
-// The local Grams run nlanes at a time: each is chunked for its share of the SMs
-// (chunking one for the whole GPU multiplies the partials its reduction reads).
-inline int local_sms(int num_sms, int nlanes) {
-  const int s = num_sms / (nlanes > 0 ? nlanes : 1);
-  return s > 0 ? s : 1;
-}
-
-// OR of the lanes' status words into info[2].
-__global__ void merge_info_kernel(const int* __restrict__ lane_info, int nlanes, int* __restrict__ info) {
+// OR of the blocks' status words into info[2] (info = block 0's words).
+__global__ void merge_info_kernel(const int* __restrict__ block_info, int nblocks,
+                                  int* __restrict__ info) {
   int bits = 0;
-  for (int l = 0; l < nlanes; ++l) bits |= lane_info[4 * l + 2];
+  for (int l = 0; l < nblocks; ++l) bits |= block_info[4 * l + 2];
   info[2] |= bits;
 }
 
@@ -102,24 +100,24 @@ struct Grow {
   ~Grow() { cudaFree(p); }
 };
 
-struct Lane {
-  Grow<double> H, X, lam, W, S, R, E, Xn, lamJ, T64, Dnew, partial;
-  Grow<float> T, fs;
-  Grow<LevelState> ls;
-  cudaStream_t st = nullptr;
-  cudaEvent_t done = nullptr;
-};
-
 }  // namespace
 
-// Workspaces and streams of apmos_run, kept by the handle across calls so that a
-// call only enqueues work (no allocation once the sizes have been seen).
-// The launch sequence of a call (thousands of small kernels: the local solves are
-// chains of ~45 launches each) is captured into a CUDA graph; a later call with
-// the same arguments and buffers replays it with one launch.
+// Workspaces of apmos_run, kept by the handle across calls so that a call only
+// enqueues work (no allocation once the sizes have been seen), and the launch
+// sequence of a call, captured into a CUDA graph that a later call with the same
+// arguments and buffers replays with one launch.
 struct ApmosCache {
-  Lane lane[kLanes];
-  Grow<int> lane_info;
+  // batched local solves: kMaxBatch problems' workspaces (problem 0 also serves the
+  // global solve once the local ones are done)
+  Grow<double> H, X, lam, W, S, R, E, Xn, lamJ, partial, Tg64, Dg;
+  Grow<float> T, fs;
+  Grow<LevelState> ls;
+  Grow<int> info;  // 4 words per problem
+  Grow<GramItem> items;
+  Grow<int> first;  // first[b]: block b's first Gram item
+  std::vector<int64_t> items_key;
+  int nitems = 0;
+  std::vector<int> first_host;
   Grow<double> T64_all, S_all, WW;
   // the randomized global SVD (low_rank): explicit W, X diag(1/s), RandWork arrays
   Grow<double> Wexp, Tout, rB0, rB1, rB2, rMm, rRr, rAw, rBb;
@@ -127,7 +125,6 @@ struct ApmosCache {
   Grow<int> rpiv, rrank;
   int low_rank = 0, p = 0, q = 0;  // this call's settings (read by apmos_enqueue)
   uint64_t seed = 0;
-  cudaEvent_t fork = nullptr;
   // the sequence is captured and replayed on this stream (capture cannot start
   // on the legacy default stream); it is ordered after and before the caller's
   cudaStream_t origin = nullptr;
@@ -136,11 +133,6 @@ struct ApmosCache {
   std::vector<int64_t> key;  // arguments and buffer addresses the graph was captured with
   ~ApmosCache() {
     if (exec) cudaGraphExecDestroy(exec);
-    for (Lane& l : lane) {
-      if (l.st) cudaStreamDestroy(l.st);
-      if (l.done) cudaEventDestroy(l.done);
-    }
-    if (fork) cudaEventDestroy(fork);
     if (origin) cudaStreamDestroy(origin);
     if (in) cudaEventDestroy(in);
     if (out) cudaEventDestroy(out);
@@ -148,150 +140,46 @@ struct ApmosCache {
 };
 
 ApmosCache* apmos_cache_create() { return new (std::nothrow) ApmosCache(); }
-
-int apmos_enqueue(ApmosCache* c, const std::vector<SmallWork>& lw, int nlanes, const void* A,
-                  size_t es, int64_t lda, int a_bf16, int64_t Mtot, const int64_t* off, int nparts,
-                  int N, int r1, int r2, float* U, int64_t ldu, double* L, int num_sms,
-                  cudaStream_t st);
 void apmos_cache_destroy(ApmosCache* c) { delete c; }
 
-int apmos_run(const void* A, int64_t lda, int a_bf16, int64_t Mtot, const int64_t* off, int nparts,
-              int N, int r1, int r2, float* U, int64_t ldu, double* L, int num_sms,
-              cudaStream_t st, ApmosCache* c, int low_rank, int p, int q, uint64_t seed,
-              int* status) {
-  if (!c) return PSVD_ERR_INVALID_ARG;
-  c->low_rank = low_rank ? 1 : 0;
-  c->p = p;
-  c->q = q;
-  c->seed = seed;
-  const size_t es = a_bf16 ? 2 : 4;
-  const size_t nn = (size_t)N * N;
-  const int nlanes = nparts < kLanes ? nparts : kLanes;
-  int64_t pmax = 0;
-  for (int b = 0; b < nparts; ++b) {
-    int nchunk;
-    int64_t rpc, pd;
-    gram_simt_plan(off[b + 1] - off[b], N, local_sms(num_sms, nlanes), &nchunk, &rpc, &pd);
-    if (pd > pmax) pmax = pd;
-  }
-  // growing a buffer frees the old one: nothing may still be using it
-  if (cudaStreamSynchronize(st) != cudaSuccess) return PSVD_ERR_CUDA;
-  bool ok = c->lane_info.ensure(4 * (size_t)nlanes) && c->T64_all.ensure((size_t)nparts * N * r1) &&
-            c->S_all.ensure((size_t)nparts * r1) && c->WW.ensure(nn);
-  std::vector<SmallWork> lw(nlanes);
-  for (int l = 0; l < nlanes && ok; ++l) {
-    Lane& ln = c->lane[l];
-    ok = ln.H.ensure(nn) && ln.X.ensure(nn) && ln.lam.ensure(N) && ln.W.ensure(nn) &&
-         ln.S.ensure(nn) && ln.R.ensure(nn) && ln.E.ensure(nn) && ln.Xn.ensure(nn) &&
-         ln.lamJ.ensure(N) && ln.T.ensure(nn) && ln.T64.ensure(nn) && ln.Dnew.ensure(N) &&
-         ln.ls.ensure(1) && ln.fs.ensure(eig_levels_scratch_floats(N)) &&
-         ln.partial.ensure((size_t)pmax);
-    if (ok && !ln.st) ok = cudaStreamCreateWithFlags(&ln.st, cudaStreamNonBlocking) == cudaSuccess;
-    if (ok && !ln.done) ok = cudaEventCreateWithFlags(&ln.done, cudaEventDisableTiming) == cudaSuccess;
-    SmallWork& w = lw[l];
-    w = SmallWork{};
-    w.H = ln.H.p;
-    w.X = ln.X.p;
-    w.lam = ln.lam.p;
-    w.W = ln.W.p;
-    w.S = ln.S.p;
-    w.R = ln.R.p;
-    w.E = ln.E.p;
-    w.Xn = ln.Xn.p;
-    w.lamJ = ln.lamJ.p;
-    w.T = ln.T.p;
-    w.T64 = ln.T64.p;
-    w.Dnew = ln.Dnew.p;
-    w.info = c->lane_info.p + 4 * l;
-    w.ls = ln.ls.p;
-    w.fs = ln.fs.p;
-  }
-  if (ok && c->low_rank) {
-    const size_t m = (size_t)r1 * nparts, lmax = (size_t)N;
-    ok = c->Wexp.ensure((size_t)N * m) && c->Tout.ensure((size_t)N * r2) &&
-         c->rB0.ensure(std::max(m, (size_t)N) * lmax) && c->rB1.ensure((size_t)N * lmax) &&
-         c->rB2.ensure((size_t)N * lmax) && c->rMm.ensure(lmax * lmax) &&
-         c->rRr.ensure(lmax * lmax) && c->rAw.ensure(lmax * lmax) && c->rBb.ensure(lmax * lmax) &&
-         c->rOm.ensure(m * lmax) && c->rpiv.ensure(lmax) && c->rrank.ensure(1);
-  }
-  if (ok && !c->fork) ok = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) == cudaSuccess;
-  if (ok && !c->origin) ok = cudaStreamCreateWithFlags(&c->origin, cudaStreamNonBlocking) == cudaSuccess;
-  if (ok && !c->in) ok = cudaEventCreateWithFlags(&c->in, cudaEventDisableTiming) == cudaSuccess;
-  if (ok && !c->out) ok = cudaEventCreateWithFlags(&c->out, cudaEventDisableTiming) == cudaSuccess;
-  if (!ok) {
-    cudaGetLastError();
-    return PSVD_ERR_ALLOC;
-  }
-#define ACK(x)                                    \
-  do {                                            \
-    if ((x) != cudaSuccess) {                     \
-      cudaGetLastError();                         \
-      return PSVD_ERR_CUDA;                       \
-    }                                             \
-  } while (0)
-  int* lane_info = c->lane_info.p;
-  double* T64_all = c->T64_all.p;  // block b's N x r1 factor
-  double* WW = c->WW.p;
-  std::vector<int64_t> key = {(int64_t)(uintptr_t)A, lda, a_bf16, Mtot, nparts, N, r1, r2,
-                              (int64_t)(uintptr_t)U, ldu, (int64_t)(uintptr_t)L, num_sms,
-                              (int64_t)(uintptr_t)st, (int64_t)(uintptr_t)lane_info,
-                              (int64_t)(uintptr_t)T64_all, (int64_t)(uintptr_t)WW};
-  for (int b = 0; b <= nparts; ++b) key.push_back(off[b]);
-  for (int l = 0; l < nlanes; ++l) key.push_back((int64_t)(uintptr_t)c->lane[l].partial.p);
-  key.push_back(c->low_rank);
-  if (c->low_rank) {
-    for (int64_t v : {(int64_t)c->p, (int64_t)c->q, (int64_t)c->seed,
-                      (int64_t)(uintptr_t)c->Wexp.p, (int64_t)(uintptr_t)c->rB0.p,
-                      (int64_t)(uintptr_t)c->rOm.p})
-      key.push_back(v);
-  }
-  // origin runs after the work already on st
-  cudaStream_t o = c->origin;
-  ACK(cudaEventRecord(c->in, st));
-  ACK(cudaStreamWaitEvent(o, c->in, 0));
-  if (!(c->exec && key == c->key)) {
-    if (c->exec) {
-      cudaGraphExecDestroy(c->exec);
-      c->exec = nullptr;
-    }
-    c->key.clear();
-    cudaGraph_t graph = nullptr;
-    if (cudaStreamBeginCapture(o, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
-      const int rc = apmos_enqueue(c, lw, nlanes, A, es, lda, a_bf16, Mtot, off, nparts, N, r1, r2,
-                                   U, ldu, L, num_sms, o);
-      const cudaError_t ec = cudaStreamEndCapture(o, &graph);
-      if (rc == PSVD_OK && ec == cudaSuccess && graph &&
-          cudaGraphInstantiate(&c->exec, graph, 0) == cudaSuccess)
-        c->key = key;
-      else
-        c->exec = nullptr;
-      if (graph) cudaGraphDestroy(graph);
-    }
-    cudaGetLastError();
-  }
-  if (c->exec) {
-    ACK(cudaGraphLaunch(c->exec, o));
-  } else {
-    // no graph (capture unavailable): enqueue the sequence directly
-    if (int rc = apmos_enqueue(c, lw, nlanes, A, es, lda, a_bf16, Mtot, off, nparts, N, r1, r2, U,
-                               ldu, L, num_sms, o))
-      return rc;
-  }
-  ACK(cudaEventRecord(c->out, o));
-  ACK(cudaStreamWaitEvent(st, c->out, 0));
-  int info[4] = {0, 0, 0, 0};
-  ACK(cudaMemcpyAsync(info, lane_info, sizeof(info), cudaMemcpyDeviceToHost, st));
-  ACK(cudaStreamSynchronize(st));
-#undef ACK
-  *status = info[2];
-  return PSVD_OK;
+namespace {
+
+// SmallWork of problems [z0, z0 + count) of the batch workspace (problem stride nn).
+SmallWork batch_work(ApmosCache* c, int N, int z0, int count, double* T64, int64_t sT64,
+                     double* Dnew, int64_t sDnew) {
+  const int64_t nn = (int64_t)N * N;
+  const int64_t fsz = (int64_t)eig_levels_scratch_floats(N);
+  SmallWork w{};
+  w.H = c->H.p;
+  w.X = c->X.p;
+  w.lam = c->lam.p;
+  w.W = c->W.p;
+  w.S = c->S.p;
+  w.R = c->R.p;
+  w.E = c->E.p;
+  w.Xn = c->Xn.p;
+  w.lamJ = c->lamJ.p;
+  w.T = c->T.p;
+  w.T64 = T64;
+  w.Dnew = Dnew;
+  w.info = c->info.p + 4 * (int64_t)z0;
+  w.ls = c->ls.p;
+  w.fs = c->fs.p;
+  w.bat.count = count;
+  w.bat.nn = nn;
+  w.bat.n = N;
+  w.bat.T = nn;
+  w.bat.T64 = sT64;
+  w.bat.Dnew = sDnew;
+  w.bat.info = 4;
+  w.bat.ls = 1;
+  w.bat.fs = fsz;
+  return w;
 }
 
-// Enqueues one APMOS run on st and the lanes' streams (captured by the caller).
-int apmos_enqueue(ApmosCache* c, const std::vector<SmallWork>& lw, int nlanes, const void* A,
-                  size_t es, int64_t lda, int a_bf16, int64_t Mtot, const int64_t* off, int nparts,
-                  int N, int r1, int r2, float* U, int64_t ldu, double* L, int num_sms,
-                  cudaStream_t st) {
+// Enqueues one APMOS run on st (captured by the caller).
+int apmos_enqueue(ApmosCache* c, const void* A, int64_t lda, int a_bf16, int64_t Mtot, int nparts,
+                  int N, int r1, int r2, float* U, int64_t ldu, double* L, cudaStream_t st) {
 #define ACK(x)                  \
   do {                          \
     if ((x) != cudaSuccess) {   \
@@ -299,44 +187,32 @@ int apmos_enqueue(ApmosCache* c, const std::vector<SmallWork>& lw, int nlanes, c
       return PSVD_ERR_CUDA;     \
     }                           \
   } while (0)
-  const size_t nn = (size_t)N * N;
-  int* lane_info = c->lane_info.p;
+  const int64_t nn = (int64_t)N * N;
   double* T64_all = c->T64_all.p;
   double* S_all = c->S_all.p;
   double* WW = c->WW.p;
-  ACK(cudaMemsetAsync(lane_info, 0, sizeof(int) * 4 * nlanes, st));
-  // fork: every lane starts after the work already on st
-  ACK(cudaEventRecord(c->fork, st));
-  for (int l = 0; l < nlanes; ++l) ACK(cudaStreamWaitEvent(c->lane[l].st, c->fork, 0));
-  int nl = 0;
-  for (int b = 0; b < nparts; ++b) {
-    // local block: Gram, eigen-decomposition, factor V~ S~ into slot b
-    const int l = b % nlanes;
-    Lane& ln = c->lane[l];
-    SmallWork w = lw[l];
-    w.T64 = T64_all + (size_t)b * N * r1;
-    w.Dnew = S_all + (size_t)b * r1;
-    const int64_t mb = off[b + 1] - off[b];
-    const void* Ab = static_cast<const char*>(A) + (size_t)off[b] * es;
-    PanelF32 p{nullptr, 0, 0, Ab, lda, a_bf16, mb, N};
-    int nchunk;
-    int64_t rpc, pd;
-    gram_simt_plan(mb, N, local_sms(num_sms, nlanes), &nchunk, &rpc, &pd);
-    ACK(gram_simt_launch(p, nchunk, rpc, ln.partial.p, ln.st));
-    ACK(gram_reduce_launch(ln.partial.p, nchunk, N, 0, nullptr, 1.0, nullptr, w.H, w.info, ln.st));
-    ACK(small_solve_launch(w, N, 0, r1, nullptr, 1.0, 3, kMaxLevels, ln.st, &nl));
-  }
-  // join, then W W^T in block order
-  for (int l = 0; l < nlanes; ++l) {
-    ACK(cudaEventRecord(c->lane[l].done, c->lane[l].st));
-    ACK(cudaStreamWaitEvent(st, c->lane[l].done, 0));
-  }
-  SmallWork w = lw[0];
-  wwt_kernel<<<(unsigned)ceil_div((int64_t)nn, 256), 256, 0, st>>>(N, r1, nparts, T64_all, S_all, WW);
-  ACK(cudaGetLastError());
-  merge_info_kernel<<<1, 1, 0, st>>>(lane_info, nlanes, lane_info);
-  ACK(cudaGetLastError());
+  const int nb = std::min(nparts, kMaxBatch);
+  ACK(cudaMemsetAsync(c->info.p, 0, sizeof(int) * 4 * nb, st));
+  // local Grams of every block: one launch over the work list of row chunks
   PanelF32 pa{nullptr, 0, 0, A, lda, a_bf16, Mtot, N};
+  ACK(gram_items_launch(pa, c->items.p, c->nitems, c->partial.p, st));
+  int nl = 0;
+  for (int z0 = 0; z0 < nparts; z0 += kMaxBatch) {
+    const int cnt = std::min(kMaxBatch, nparts - z0);
+    // H_b for the blocks of this batch, then their eigen-solves side by side;
+    // block b's factor goes to slot b of T64_all / S_all
+    ACK(gram_reduce_items_launch(c->partial.p, c->first.p + z0, cnt, N, c->H.p, nn, c->info.p, st));
+    SmallWork w = batch_work(c, N, 0, cnt, T64_all + (int64_t)z0 * N * r1, (int64_t)N * r1,
+                             S_all + (int64_t)z0 * r1, r1);
+    ACK(small_solve_launch(w, N, 0, r1, nullptr, 1.0, 3, kMaxLevels, st, &nl));
+    merge_info_kernel<<<1, 1, 0, st>>>(c->info.p, cnt, c->info.p);
+    ACK(cudaGetLastError());
+  }
+  // W W^T in block order
+  wwt_kernel<<<(unsigned)ceil_div(nn, 256), 256, 0, st>>>(N, r1, nparts, T64_all, S_all, WW);
+  ACK(cudaGetLastError());
+  // the global solve on problem 0's workspace (its status words collect every block's)
+  SmallWork w = batch_work(c, N, 0, 1, c->Tg64.p, 0, c->Dg.p, 0);
   if (c->low_rank) {
     // global: the paper's low_rank_svd of the explicit W, T = X~ diag(1/L~), U = A T
     const int m = r1 * nparts;
@@ -362,12 +238,138 @@ int apmos_enqueue(ApmosCache* c, const std::vector<SmallWork>& lw, int nlanes, c
     ACK(cudaGetLastError());
   } else {
     // global: eigen-decomposition of W W^T, T = X~ diag(1/L~), U = A T
+    w.T64 = nullptr;
     ACK(cudaMemcpyAsync(w.H, WW, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st));
     ACK(small_solve_launch(w, N, 0, r2, nullptr, 1.0, 3, kMaxLevels, st, &nl));
   }
   ACK(update_simt_launch(pa, w.T, r2, U, ldu, st));
   ACK(cudaMemcpyAsync(L, w.Dnew, sizeof(double) * r2, cudaMemcpyDeviceToDevice, st));
 #undef ACK
+  return PSVD_OK;
+}
+
+}  // namespace
+
+int apmos_run(const void* A, int64_t lda, int a_bf16, int64_t Mtot, const int64_t* off, int nparts,
+              int N, int r1, int r2, float* U, int64_t ldu, double* L, int num_sms,
+              cudaStream_t st, ApmosCache* c, int low_rank, int p, int q, uint64_t seed,
+              int* status) {
+  if (!c) return PSVD_ERR_INVALID_ARG;
+  c->low_rank = low_rank ? 1 : 0;
+  c->p = p;
+  c->q = q;
+  c->seed = seed;
+  const size_t nn = (size_t)N * N;
+  const int nb = std::min(nparts, kMaxBatch);
+  // the Gram work list of these blocks (rebuilt when the blocks change)
+  std::vector<int64_t> ikey(off, off + nparts + 1);
+  ikey.push_back(N);
+  ikey.push_back(num_sms);
+  std::vector<GramItem> items;
+  int64_t pdoubles = 0;
+  const bool new_items = ikey != c->items_key;
+  if (new_items) gram_items_plan(off, nparts, N, num_sms, &items, &c->first_host, &pdoubles);
+  // growing a buffer frees the old one: nothing may still be using it
+  if (cudaStreamSynchronize(st) != cudaSuccess) return PSVD_ERR_CUDA;
+  const size_t fsz = eig_levels_scratch_floats(N);
+  bool ok = c->T64_all.ensure((size_t)nparts * N * r1) && c->S_all.ensure((size_t)nparts * r1) &&
+            c->WW.ensure(nn) && c->H.ensure(nb * nn) && c->X.ensure(nb * nn) &&
+            c->lam.ensure((size_t)nb * N) && c->W.ensure(nb * nn) && c->S.ensure(nb * nn) &&
+            c->R.ensure(nb * nn) && c->E.ensure(nb * nn) && c->Xn.ensure(nb * nn) &&
+            c->lamJ.ensure((size_t)nb * N) && c->T.ensure(nb * nn) && c->Tg64.ensure(nn) &&
+            c->Dg.ensure(N) && c->ls.ensure(nb) && c->fs.ensure(nb * fsz) &&
+            c->info.ensure(4 * (size_t)nb);
+  if (ok && new_items) {
+    c->items_key.clear();
+    ok = c->items.ensure(items.size()) && c->first.ensure(c->first_host.size()) &&
+         c->partial.ensure((size_t)pdoubles) &&
+         cudaMemcpy(c->items.p, items.data(), sizeof(GramItem) * items.size(),
+                    cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(c->first.p, c->first_host.data(), sizeof(int) * c->first_host.size(),
+                    cudaMemcpyHostToDevice) == cudaSuccess;
+    if (ok) {
+      c->nitems = (int)items.size();
+      c->items_key = ikey;
+    }
+  }
+  if (ok && c->low_rank) {
+    const size_t m = (size_t)r1 * nparts, lmax = (size_t)N;
+    ok = c->Wexp.ensure((size_t)N * m) && c->Tout.ensure((size_t)N * r2) &&
+         c->rB0.ensure(std::max(m, (size_t)N) * lmax) && c->rB1.ensure((size_t)N * lmax) &&
+         c->rB2.ensure((size_t)N * lmax) && c->rMm.ensure(lmax * lmax) &&
+         c->rRr.ensure(lmax * lmax) && c->rAw.ensure(lmax * lmax) && c->rBb.ensure(lmax * lmax) &&
+         c->rOm.ensure(m * lmax) && c->rpiv.ensure(lmax) && c->rrank.ensure(1);
+  }
+  if (ok && !c->origin) ok = cudaStreamCreateWithFlags(&c->origin, cudaStreamNonBlocking) == cudaSuccess;
+  if (ok && !c->in) ok = cudaEventCreateWithFlags(&c->in, cudaEventDisableTiming) == cudaSuccess;
+  if (ok && !c->out) ok = cudaEventCreateWithFlags(&c->out, cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    return PSVD_ERR_ALLOC;
+  }
+#define ACK(x)                                    \
+  do {                                            \
+    if ((x) != cudaSuccess) {                     \
+      cudaGetLastError();                         \
+      return PSVD_ERR_CUDA;                       \
+    }                                             \
+  } while (0)
+  std::vector<int64_t> key = {(int64_t)(uintptr_t)A, lda, a_bf16, Mtot, nparts, N, r1, r2,
+                              (int64_t)(uintptr_t)U, ldu, (int64_t)(uintptr_t)L, num_sms,
+                              (int64_t)(uintptr_t)st, c->nitems};
+  for (const void* ptr : {(const void*)c->info.p, (const void*)c->T64_all.p, (const void*)c->S_all.p,
+                          (const void*)c->WW.p, (const void*)c->H.p, (const void*)c->X.p,
+                          (const void*)c->lam.p, (const void*)c->W.p, (const void*)c->S.p,
+                          (const void*)c->R.p, (const void*)c->E.p, (const void*)c->Xn.p,
+                          (const void*)c->lamJ.p, (const void*)c->T.p, (const void*)c->Tg64.p,
+                          (const void*)c->Dg.p, (const void*)c->ls.p, (const void*)c->fs.p,
+                          (const void*)c->items.p, (const void*)c->first.p,
+                          (const void*)c->partial.p})
+    key.push_back((int64_t)(uintptr_t)ptr);
+  for (int b = 0; b <= nparts; ++b) key.push_back(off[b]);
+  key.push_back(c->low_rank);
+  if (c->low_rank) {
+    for (int64_t v : {(int64_t)c->p, (int64_t)c->q, (int64_t)c->seed,
+                      (int64_t)(uintptr_t)c->Wexp.p, (int64_t)(uintptr_t)c->rB0.p,
+                      (int64_t)(uintptr_t)c->rOm.p})
+      key.push_back(v);
+  }
+  // origin runs after the work already on st
+  cudaStream_t o = c->origin;
+  ACK(cudaEventRecord(c->in, st));
+  ACK(cudaStreamWaitEvent(o, c->in, 0));
+  if (!(c->exec && key == c->key)) {
+    if (c->exec) {
+      cudaGraphExecDestroy(c->exec);
+      c->exec = nullptr;
+    }
+    c->key.clear();
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(o, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+      const int rc = apmos_enqueue(c, A, lda, a_bf16, Mtot, nparts, N, r1, r2, U, ldu, L, o);
+      const cudaError_t ec = cudaStreamEndCapture(o, &graph);
+      if (rc == PSVD_OK && ec == cudaSuccess && graph &&
+          cudaGraphInstantiate(&c->exec, graph, 0) == cudaSuccess)
+        c->key = key;
+      else
+        c->exec = nullptr;
+      if (graph) cudaGraphDestroy(graph);
+    }
+    cudaGetLastError();
+  }
+  if (c->exec) {
+    ACK(cudaGraphLaunch(c->exec, o));
+  } else {
+    // no graph (capture unavailable): enqueue the sequence directly
+    if (int rc = apmos_enqueue(c, A, lda, a_bf16, Mtot, nparts, N, r1, r2, U, ldu, L, o)) return rc;
+  }
+  ACK(cudaEventRecord(c->out, o));
+  ACK(cudaStreamWaitEvent(st, c->out, 0));
+  int info[4] = {0, 0, 0, 0};
+  ACK(cudaMemcpyAsync(info, c->info.p, sizeof(info), cudaMemcpyDeviceToHost, st));
+  ACK(cudaStreamSynchronize(st));
+#undef ACK
+  *status = info[2];
   return PSVD_OK;
 }
 

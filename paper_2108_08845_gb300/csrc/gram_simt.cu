@@ -14,6 +14,8 @@
 // (relative error ~ u * fold_rows / sqrt(M), kept near 1e-9).
 #include <math.h>
 
+#include <vector>
+
 #include "psvd_internal.cuh"
 
 namespace psvd {
@@ -49,9 +51,13 @@ __device__ __forceinline__ void decode_pair(int pair, int nb, int* bi, int* bj) 
   *bj = i + pair;
 }
 
+// Row chunk blockIdx.y: rows [blockIdx.y * rows_per_chunk, ...) of the panel, or,
+// with a work list, rows [items[y].r0, items[y].r1) with that item's chain length
+// (the row blocks of Algorithm 2 in one launch).
 __global__ void __launch_bounds__(GTHREADS) gram_partial_kernel(PanelF32 p, int nb,
                                                                 int64_t rows_per_chunk,
                                                                 int fold_steps,
+                                                                const GramItem* __restrict__ items,
                                                                 double* __restrict__ partial) {
   __shared__ __align__(16) float Xi[GB * GLD];
   __shared__ __align__(16) float Xj[GB * GLD];
@@ -59,8 +65,14 @@ __global__ void __launch_bounds__(GTHREADS) gram_partial_kernel(PanelF32 p, int 
   decode_pair(blockIdx.x, nb, &bi, &bj);
   const bool diag = (bi == bj);
   const int npairs = gridDim.x;
-  const int64_t r_begin = (int64_t)blockIdx.y * rows_per_chunk;
-  const int64_t r_end = min(p.M, r_begin + rows_per_chunk);
+  int64_t r_begin = (int64_t)blockIdx.y * rows_per_chunk;
+  int64_t r_end = min(p.M, r_begin + rows_per_chunk);
+  if (items) {
+    const GramItem it = items[blockIdx.y];
+    r_begin = it.r0;
+    r_end = it.r1;
+    fold_steps = it.fold_steps;
+  }
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, lane = tid & 31, warp = tid >> 5;
 
   float acc[4][4], hi[4][4], lo[4][4];
@@ -247,7 +259,70 @@ cudaError_t gram_simt_launch(const PanelF32& p, int nchunk, int64_t rows_per_chu
   const int nb = (int)ceil_div(p.n, GB);
   dim3 grid(nb * (nb + 1) / 2, nchunk);
   gram_partial_kernel<<<grid, GTHREADS, 0, st>>>(p, nb, rows_per_chunk,
-                                                 gram_simt_fold_steps(p.M), partial);
+                                                 gram_simt_fold_steps(p.M), nullptr, partial);
+  return cudaGetLastError();
+}
+
+void gram_items_plan(const int64_t* off, int nparts, int n, int num_sms, std::vector<GramItem>* items,
+                     std::vector<int>* first, int64_t* partial_doubles) {
+  const int nb = (int)ceil_div(n, GB);
+  const int npairs = nb * (nb + 1) / 2;
+  const int64_t total = off[nparts] - off[0];
+  // about 4 CTAs per SM over all blocks, chunks a multiple of the stage height
+  int64_t want = (int64_t)num_sms * 4 / npairs;
+  if (want < 1) want = 1;
+  int64_t rpc = ceil_div(ceil_div(total, want), GRS) * GRS;
+  if (rpc < GRS) rpc = GRS;
+  items->clear();
+  first->assign(nparts + 1, 0);
+  for (int b = 0; b < nparts; ++b) {
+    (*first)[b] = (int)items->size();
+    const int64_t mb = off[b + 1] - off[b];
+    const int fs = gram_simt_fold_steps(mb);  // the chain length of a lone Gram of this block
+    for (int64_t r = off[b]; r < off[b + 1]; r += rpc)
+      items->push_back(GramItem{r, r + rpc < off[b + 1] ? r + rpc : off[b + 1], fs});
+  }
+  (*first)[nparts] = (int)items->size();
+  *partial_doubles = (int64_t)items->size() * npairs * GB * GB;
+}
+
+cudaError_t gram_items_launch(const PanelF32& p, const GramItem* items, int nitems, double* partial,
+                              cudaStream_t st) {
+  const int nb = (int)ceil_div(p.n, GB);
+  dim3 grid(nb * (nb + 1) / 2, nitems);
+  gram_partial_kernel<<<grid, GTHREADS, 0, st>>>(p, nb, 0, 1, items, partial);
+  return cudaGetLastError();
+}
+
+// H_z = sum of the partials of items [first[z], first[z+1]) (fixed order), z < count;
+// H_z at H + z * sH (n x n), info_z at info + 4 z.
+__global__ void gram_reduce_items_kernel(const double* __restrict__ partial,
+                                         const int* __restrict__ first, int nb, int n,
+                                         double* __restrict__ H, int64_t sH, int* __restrict__ info) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int z = blockIdx.y;
+  if (e >= (int64_t)n * n) return;
+  int i = (int)(e % n), j = (int)(e / n);
+  int bi = i / GB, bj = j / GB, il = i % GB, jl = j % GB;
+  if (bi > bj || (bi == bj && il > jl)) {
+    int t = bi; bi = bj; bj = t;
+    t = il; il = jl; jl = t;
+  }
+  const int npairs = nb * (nb + 1) / 2;
+  const int pair = bi * nb - bi * (bi - 1) / 2 + (bj - bi);
+  double s = 0.0;
+  for (int c = first[z]; c < first[z + 1]; ++c)
+    s += partial[((size_t)c * npairs + pair) * (GB * GB) + il + GB * jl];
+  H[z * sH + e] = s;
+  if (!isfinite(s)) atomicOr(&info[4 * z + 2], 4);
+}
+
+cudaError_t gram_reduce_items_launch(const double* partial, const int* first, int count, int n,
+                                     double* H, int64_t sH, int* info, cudaStream_t st) {
+  const int nb = (int)ceil_div(n, GB);
+  const int64_t tot = (int64_t)n * n;
+  gram_reduce_items_kernel<<<dim3((unsigned)ceil_div(tot, 256), (unsigned)count), 256, 0, st>>>(
+      partial, first, nb, n, H, sH, info);
   return cudaGetLastError();
 }
 

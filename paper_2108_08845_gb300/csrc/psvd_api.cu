@@ -331,6 +331,10 @@ int time_ms(cudaStream_t st, int reps, F fn, float* ms) {
 
 extern "C" {
 
+int psvd_debug_set_wait_budget(int32_t kernel, int64_t cycles) {
+  return tc_set_wait_budget(kernel, (long long)cycles);
+}
+
 const char* psvd_status_string(int s) {
   switch (s) {
     case PSVD_OK: return "ok";

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "psvd.h"
 
 namespace psvd {
@@ -42,6 +44,23 @@ void gram_simt_plan(int64_t M, int n, int num_sms, int* nchunk, int64_t* rows_pe
 // Partial Grams of the panel over row chunks (FP64 per chunk, float-float inside).
 cudaError_t gram_simt_launch(const PanelF32& p, int nchunk, int64_t rows_per_chunk,
                              double* partial, cudaStream_t st);
+// Gram of row blocks of one panel in one launch (Algorithm 2's local Grams): a work
+// list of row chunks [r0, r1) with the chain length of their block.
+struct GramItem {
+  int64_t r0, r1;
+  int fold_steps;
+};
+// Chunks for the row blocks [off[b], off[b+1]) of an n-column panel, about 4 CTAs per
+// SM in all; first[b] is block b's first item (first[nparts] = the item count).
+void gram_items_plan(const int64_t* off, int nparts, int n, int num_sms, std::vector<GramItem>* items,
+                     std::vector<int>* first, int64_t* partial_doubles);
+// Partials of the items (device work list) of the panel p (p.M = all rows).
+cudaError_t gram_items_launch(const PanelF32& p, const GramItem* items, int nitems, double* partial,
+                              cudaStream_t st);
+// H_z (n x n, stride sH) = fixed-order sum of the partials of items [first[z], first[z+1])
+// (first: device array), z < count; non-finite entries set bit 4 of info[4 z + 2].
+cudaError_t gram_reduce_items_launch(const double* partial, const int* first, int count, int n,
+                                     double* H, int64_t sH, int* info, cudaStream_t st);
 // G = sum of partials (fixed order), H = S G S with S = diag(ff*D[0:kc], 1).
 // G may be null.  ldg = ldh = n.  A non-finite Gram entry sets info[2] bit 4.
 cudaError_t gram_reduce_launch(const double* partial, int nchunk, int n, int kc,
@@ -94,6 +113,21 @@ struct LevelState {
   double lmax;  // largest eigenvalue of H
 };
 
+// Batched small solves: `count` independent problems of the same size, problem z's
+// arrays at the SmallWork pointers plus z times these element strides (count = 1:
+// one problem, strides unused).
+struct SmallBatch {
+  int count = 1;
+  int64_t nn = 0;    // H, X, W, S, R, E, Xn (each n x n)
+  int64_t n = 0;     // lam, lamJ
+  int64_t T = 0;     // T (FP32)
+  int64_t T64 = 0;   // T64
+  int64_t Dnew = 0;  // Dnew
+  int64_t info = 0;  // info (ints)
+  int64_t ls = 0;    // ls (LevelState elements)
+  int64_t fs = 0;    // fs (floats)
+};
+
 struct SmallWork {
   double* H;      // n x n FP64 (scaled Gram), ld n
   double* X;      // n x n FP64 eigenvector estimates (sorted), ld n
@@ -115,6 +149,7 @@ struct SmallWork {
   // resolved (modes zeroed, PSVD_WARN_RANK_DEFICIENT).  0 means 1e-9 (the FP32 and
   // tensor-core Grams); FP64 Grams resolve far deeper.
   double lam_floor;
+  SmallBatch bat;  // several problems in each launch (small_solve_launch)
 };
 __host__ __device__ inline double lambda_floor(const SmallWork& w) {
   return w.lam_floor > 0.0 ? w.lam_floor : 1e-9;
@@ -134,10 +169,14 @@ cudaError_t small_solve_launch(const SmallWork& w, int n, int kc, int k1, const 
 cudaError_t eig_levels_launch(const SmallWork& w, int n, int nJ, int max_levels, cudaStream_t st,
                               int* launches);
 size_t eig_levels_scratch_floats(int nmax);
-// C (m x nn) = op(A) * B (FP64) if *flag != 0, otherwise nothing.
-cudaError_t dgemm_flag_launch(bool trans_a, int m, int nn, int k, const double* A, int lda,
-                              const double* B, int ldb, double* C, int ldc, const int* flag,
-                              cudaStream_t st);
+// Batched FP64 GEMM: for z < count, C_z (m x nn) = alpha op(A_z) B_z + beta Cin_z with
+// X_z = X + z * sX (element strides), skipped for problem z when ls != null and
+// ls[z * sls].active == 0.
+cudaError_t dgemm_batched_launch(bool trans_a, int m, int nn, int k, double alpha, const double* A,
+                                 int lda, int64_t sA, const double* B, int ldb, int64_t sB,
+                                 double beta, const double* Cin, int ldci, int64_t sCin, double* C,
+                                 int ldc, int64_t sC, const LevelState* ls, int64_t sls, int count,
+                                 cudaStream_t st);
 // C (m x nn) = alpha * op(A) * B + beta * Cin (FP64, column-major), op(A) = A or A^T.
 cudaError_t dgemm_launch(bool trans_a, int m, int nn, int k, double alpha, const double* A, int lda,
                          const double* B, int ldb, double beta, const double* Cin, int ldci,

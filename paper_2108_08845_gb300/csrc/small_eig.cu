@@ -76,9 +76,22 @@ struct LevelArgs {
   double tau;         // resolved: lambda >= tau * lambda_max(level)
   double floor_rel;   // stop once lambda_max(level) <= floor_rel * lambda_max(H)
   double ctol;        // cluster: consecutive eigenvalues closer than ctol * ||T||
+  // batch: CTA z solves problem z, its arrays offset by z times these strides
+  int64_t sHf, sLam, sFs, sLs;
 };
 
-__global__ void __launch_bounds__(LT) level_eig_kernel(LevelArgs a) {
+__global__ void __launch_bounds__(LT) level_eig_kernel(LevelArgs a0) {
+  // problem blockIdx.x of a batch
+  LevelArgs a = a0;
+  {
+    const int64_t z = blockIdx.x;
+    a.Hf += z * a0.sHf;
+    a.lam += z * a0.sLam;
+    a.Zs += z * a0.sFs;
+    a.V += z * a0.sFs;
+    a.vb += z * a0.sFs;
+    a.ls += z * a0.sLs;
+  }
   extern __shared__ __align__(16) float smem[];
   __shared__ float d[kMaxN], e[kMaxN], e2[kMaxN], lamf[kMaxN], qbeta[kMaxN];
   __shared__ float red[LW];
@@ -818,8 +831,18 @@ __global__ void __launch_bounds__(LT) level_eig_kernel(LevelArgs a) {
 constexpr int BTW = 8;  // warps (columns) per CTA of the back-transformation
 __global__ void __launch_bounds__(BTW * 32) level_backtransform_kernel(
     int n, const float* __restrict__ Zs, const float* __restrict__ V, const float* __restrict__ vb,
-    double* __restrict__ Y, const LevelState* __restrict__ ls, int first) {
+    double* __restrict__ Y, const LevelState* __restrict__ ls, int first, int64_t sFs, int64_t sY,
+    int64_t sLs) {
   extern __shared__ __align__(16) float vs[];  // m x m reflectors (ld m), then m coefficients
+  {
+    // problem blockIdx.y of a batch
+    const int64_t z = blockIdx.y;
+    Zs += z * sFs;
+    V += z * sFs;
+    vb += z * sFs;
+    Y += z * sY;
+    ls += z * sLs;
+  }
   const int lane = threadIdx.x & 31;
   const int c = blockIdx.x * BTW + (threadIdx.x >> 5);
   const bool skip = ls->skip != 0;
@@ -872,7 +895,8 @@ __global__ void __launch_bounds__(BTW * 32) level_backtransform_kernel(
   }
 }
 
-__global__ void level_init_kernel(LevelState* ls) {
+__global__ void level_init_kernel(LevelState* ls, int64_t sLs) {
+  ls += blockIdx.x * sLs;
   ls->b = 0;
   ls->active = 1;
   ls->skip = 0;
@@ -886,9 +910,18 @@ __global__ void level_init_kernel(LevelState* ls) {
 __global__ void __launch_bounds__(64) level_update_kernel(int n, const double* __restrict__ A,
                                                           const double* __restrict__ B,
                                                           double* __restrict__ C,
-                                                          const LevelState* __restrict__ ls) {
+                                                          const LevelState* __restrict__ ls,
+                                                          int64_t sNN, int64_t sLs) {
   __shared__ double As[8][33];
   __shared__ double Bs[32][9];
+  {
+    // problem blockIdx.z of a batch
+    const int64_t z = blockIdx.z;
+    A += z * sNN;
+    B += z * sNN;
+    C += z * sNN;
+    ls += z * sLs;
+  }
   const bool skip = ls->skip != 0;
   const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
   const int row = blockIdx.x * 8 + tx, col = blockIdx.y * 8 + ty;
@@ -923,6 +956,8 @@ size_t eig_levels_scratch_floats(int nmax) { return 2 * (size_t)nmax * nmax + (s
 cudaError_t eig_levels_launch(const SmallWork& w, int n, int nJ, int max_levels, cudaStream_t st,
                               int* launches) {
   cudaError_t e;
+  const SmallBatch& bs = w.bat;
+  const unsigned nb = (unsigned)bs.count;
   const size_t smem = level_smem_bytes();
   if ((e = cudaFuncSetAttribute(level_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem)) != cudaSuccess)
@@ -938,13 +973,17 @@ cudaError_t eig_levels_launch(const SmallWork& w, int n, int nJ, int max_levels,
   a.tau = 1e-3;
   a.floor_rel = lambda_floor(w);
   a.ctol = 1e-5;
+  a.sHf = bs.nn;
+  a.sLam = bs.n;
+  a.sFs = bs.fs;
+  a.sLs = bs.ls;
   int nl = 0;
-  level_init_kernel<<<1, 1, 0, st>>>(w.ls);
+  level_init_kernel<<<nb, 1, 0, st>>>(w.ls, bs.ls);
   ++nl;
   // buffers: X ping-pong between w.Xn and w.X so that the result ends in w.X
   double* cur = ((max_levels - 1) % 2 == 0) ? w.X : w.Xn;
   double* nxt = (cur == w.X) ? w.Xn : w.X;
-  const unsigned gbt = (unsigned)ceil_div(n, BTW);
+  const dim3 gbt((unsigned)ceil_div(n, BTW), nb);
   const size_t bt_smem = sizeof(float) * ((size_t)n * n + n);
   if ((e = cudaFuncSetAttribute(level_backtransform_kernel,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt_smem)) !=
@@ -953,23 +992,29 @@ cudaError_t eig_levels_launch(const SmallWork& w, int n, int nJ, int max_levels,
   // level 0 on H itself: Y_0 is X
   a.Hf = w.H;
   a.last = (max_levels == 1);
-  level_eig_kernel<<<1, LT, smem, st>>>(a);
+  level_eig_kernel<<<nb, LT, smem, st>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  level_backtransform_kernel<<<gbt, BTW * 32, bt_smem, st>>>(n, a.Zs, a.V, a.vb, cur, w.ls, 1);
+  level_backtransform_kernel<<<gbt, BTW * 32, bt_smem, st>>>(n, a.Zs, a.V, a.vb, cur, w.ls, 1,
+                                                             bs.fs, bs.nn, bs.ls);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   nl += 2;
-  const dim3 g8((unsigned)ceil_div(n, 8), (unsigned)ceil_div(n, 8));
+  const dim3 g8((unsigned)ceil_div(n, 8), (unsigned)ceil_div(n, 8), nb);
   for (int lev = 1; lev < max_levels; ++lev) {
-    // H_l = X^T H X (FP64); both products are no-ops once the levels are done
-    if ((e = dgemm_flag_launch(false, n, n, n, w.H, n, cur, n, w.W, n, &w.ls->active, st))) return e;
-    if ((e = dgemm_flag_launch(true, n, n, n, cur, n, w.W, n, w.S, n, &w.ls->active, st))) return e;
+    // H_l = X^T H X (FP64); both products are no-ops once a problem's levels are done
+    if ((e = dgemm_batched_launch(false, n, n, n, 1.0, w.H, n, bs.nn, cur, n, bs.nn, 0.0, nullptr, n,
+                                  0, w.W, n, bs.nn, w.ls, bs.ls, bs.count, st)))
+      return e;
+    if ((e = dgemm_batched_launch(true, n, n, n, 1.0, cur, n, bs.nn, w.W, n, bs.nn, 0.0, nullptr, n,
+                                  0, w.S, n, bs.nn, w.ls, bs.ls, bs.count, st)))
+      return e;
     a.Hf = w.S;
     a.last = (lev == max_levels - 1);
-    level_eig_kernel<<<1, LT, smem, st>>>(a);
+    level_eig_kernel<<<nb, LT, smem, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    level_backtransform_kernel<<<gbt, BTW * 32, bt_smem, st>>>(n, a.Zs, a.V, a.vb, w.R, w.ls, 0);
+    level_backtransform_kernel<<<gbt, BTW * 32, bt_smem, st>>>(n, a.Zs, a.V, a.vb, w.R, w.ls, 0,
+                                                               bs.fs, bs.nn, bs.ls);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    level_update_kernel<<<g8, 64, 0, st>>>(n, cur, w.R, nxt, w.ls);
+    level_update_kernel<<<g8, 64, 0, st>>>(n, cur, w.R, nxt, w.ls, bs.nn, bs.ls);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     nl += 5;
     double* t = cur;

@@ -31,16 +31,23 @@ namespace {
 __device__ __forceinline__ double sort_key(double x) { return isnan(x) ? -INFINITY : x; }
 
 // C (m x nn) = alpha * op(A) * B + beta * Cin, FP64, column-major.
-// op(A) = A (lda >= m) or A^T (A is k x m).  8 x 8 outputs per CTA.
-// With flag != nullptr the kernel does nothing while *flag == 0.
+// op(A) = A (lda >= m) or A^T (A is k x m).  8 x 8 outputs per CTA; blockIdx.z is
+// the problem of a batch (each operand offset by its stride).  With ls != nullptr
+// the kernel does nothing for a problem whose level solve is no longer active.
 template <bool TRANS_A>
-__global__ void __launch_bounds__(64) dgemm_kernel(int m, int nn, int k, double alpha,
-                                                   const double* __restrict__ A, int lda,
-                                                   const double* __restrict__ B, int ldb,
+__global__ void __launch_bounds__(64, 1) dgemm_kernel(int m, int nn, int k, double alpha,
+                                                   const double* __restrict__ A, int lda, int64_t sA,
+                                                   const double* __restrict__ B, int ldb, int64_t sB,
                                                    double beta, const double* __restrict__ Cin,
-                                                   int ldci, double* __restrict__ C, int ldc,
-                                                   const int* __restrict__ flag) {
-  if (flag && *flag == 0) return;
+                                                   int ldci, int64_t sCin, double* __restrict__ C,
+                                                   int ldc, int64_t sC,
+                                                   const LevelState* __restrict__ ls, int64_t sls) {
+  const int64_t z = blockIdx.z;
+  if (ls && ls[z * sls].active == 0) return;
+  A += z * sA;
+  B += z * sB;
+  C += z * sC;
+  if (Cin) Cin += z * sCin;
   __shared__ double As[8][33];
   __shared__ double Bs[32][9];
   const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
@@ -82,8 +89,16 @@ __global__ void __launch_bounds__(64) dgemm_kernel(int m, int nn, int k, double 
 __global__ void oa_correct_kernel(int n, int nJ, const double* __restrict__ S,
                                   const double* __restrict__ XtX, const double* __restrict__ lam,
                                   double tau, double lam_floor, double* __restrict__ E,
-                                  double* __restrict__ lamJ, int* __restrict__ info) {
+                                  double* __restrict__ lamJ, int* __restrict__ info,
+                                  SmallBatch bs) {
   const int j = blockIdx.x;
+  const int64_t z = blockIdx.y;
+  S += z * bs.nn;
+  XtX += z * bs.nn;
+  E += z * bs.nn;
+  lam += z * bs.n;
+  lamJ += z * bs.n;
+  info += z * bs.info;
   const double* Sj = S + (int64_t)j * n;
   const double* Rj = XtX + (int64_t)j * n;
   const double ltj = Sj[j] / Rj[j];
@@ -118,9 +133,14 @@ __global__ void oa_correct_kernel(int n, int nJ, const double* __restrict__ S,
 
 // lamJ[j] = x_j^T (H x_j) / x_j^T x_j for the refined columns (W = H X_J given).
 __global__ void rayleigh_kernel(int n, int nJ, const double* __restrict__ X,
-                                const double* __restrict__ W, double* __restrict__ lamJ) {
+                                const double* __restrict__ W, double* __restrict__ lamJ,
+                                SmallBatch bs) {
   __shared__ double s_num[256], s_den[256];
   const int j = blockIdx.x;
+  const int64_t z = blockIdx.y;
+  X += z * bs.nn;
+  W += z * bs.nn;
+  lamJ += z * bs.n;
   double num = 0.0, den = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const double x = X[i + (int64_t)j * n];
@@ -141,9 +161,10 @@ __global__ void rayleigh_kernel(int n, int nJ, const double* __restrict__ X,
 }
 
 __global__ void copy_cols_kernel(const double* __restrict__ src, double* __restrict__ dst,
-                                 int64_t count) {
+                                 int64_t count, int64_t stride) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < count) dst[e] = src[e];
+  const int64_t z = blockIdx.y;
+  if (e < count) dst[z * stride + e] = src[z * stride + e];
 }
 
 // Sort the refined eigenpairs, truncate to k1 and form the update coefficients.
@@ -153,7 +174,17 @@ __global__ void finalize_kernel(int n, int nJ, int kc, int k1, const double* __r
                                 const double* __restrict__ lamJ, const double* __restrict__ D,
                                 double ff, double sig_floor, float* __restrict__ T,
                                 __nv_bfloat16* __restrict__ T3, double* __restrict__ T64,
-                                double* __restrict__ Dnew, int* __restrict__ info) {
+                                double* __restrict__ Dnew, int* __restrict__ info, SmallBatch bs) {
+  {
+    // problem blockIdx.y of a batch (T3 and D are only used unbatched)
+    const int64_t z = blockIdx.y;
+    X += z * bs.nn;
+    lamJ += z * bs.n;
+    T += z * bs.T;
+    if (T64) T64 += z * bs.T64;
+    Dnew += z * bs.Dnew;
+    info += z * bs.info;
+  }
   // block b takes output columns [kFinCols b, kFinCols (b + 1)); the ordering and
   // the singular values are formed by every block (a few hundred operations)
   __shared__ int order[kMaxN];
@@ -248,18 +279,31 @@ __global__ void cholesky_kernel(const double* __restrict__ G, int n, double* __r
 }
 
 template <bool TA>
-cudaError_t dgemm(int m, int nn, int k, double alpha, const double* A, int lda, const double* B,
-                  int ldb, double beta, const double* Cin, int ldci, double* C, int ldc,
-                  cudaStream_t st, const int* flag = nullptr) {
-  dim3 grid((unsigned)ceil_div(m, 8), (unsigned)ceil_div(nn, 8));
-  dgemm_kernel<TA><<<grid, 64, 0, st>>>(m, nn, k, alpha, A, lda, B, ldb, beta, Cin, ldci, C, ldc,
-                                        flag);
+cudaError_t dgemm_b(int m, int nn, int k, double alpha, const double* A, int lda, int64_t sA,
+                    const double* B, int ldb, int64_t sB, double beta, const double* Cin, int ldci,
+                    int64_t sCin, double* C, int ldc, int64_t sC, const LevelState* ls, int64_t sls,
+                    int count, cudaStream_t st) {
+  dim3 grid((unsigned)ceil_div(m, 8), (unsigned)ceil_div(nn, 8), (unsigned)count);
+  dgemm_kernel<TA><<<grid, 64, 0, st>>>(m, nn, k, alpha, A, lda, sA, B, ldb, sB, beta, Cin, ldci,
+                                        sCin, C, ldc, sC, ls, sls);
   return cudaGetLastError();
+}
+
+// One GEMM per problem of the batch w.bat on the n x n workspaces (stride bs.nn).
+template <bool TA>
+cudaError_t dgemm_w(const SmallBatch& bs, int m, int nn, int k, double alpha, const double* A,
+                    int lda, const double* B, int ldb, double beta, const double* Cin, int ldci,
+                    double* C, int ldc, cudaStream_t st) {
+  return dgemm_b<TA>(m, nn, k, alpha, A, lda, bs.nn, B, ldb, bs.nn, beta, Cin, ldci, bs.nn, C, ldc,
+                     bs.nn, nullptr, 0, bs.count, st);
 }
 
 // info[0] = levels, info[1] = leading eigenpairs resolved; bit 2 when the levels
 // ended before resolving nJ eigenpairs above the resolution floor.
-__global__ void level_info_kernel(const LevelState* __restrict__ ls, int nJ, int* __restrict__ info) {
+__global__ void level_info_kernel(const LevelState* __restrict__ ls, int nJ, int* __restrict__ info,
+                                  SmallBatch bs) {
+  ls += blockIdx.x * bs.ls;
+  info += blockIdx.x * bs.info;
   info[0] = ls->levels;
   info[1] = ls->b;
   if (ls->b < nJ && !ls->floored) atomicOr(&info[2], 2);
@@ -271,50 +315,57 @@ cudaError_t small_solve_launch(const SmallWork& w, int n, int kc, int k1, const 
                                double ff, int refine_steps, int max_levels, cudaStream_t st,
                                int* launches) {
   cudaError_t e;
+  const SmallBatch& bs = w.bat;
+  const unsigned nb = (unsigned)bs.count;
   const int nJ = (k1 + kRefineMargin < n) ? k1 + kRefineMargin : n;
   int nl = 0;
   // 1. basis X and eigenvalue estimates lam from the scale levels
   if ((e = eig_levels_launch(w, n, nJ, max_levels, st, &nl)) != cudaSuccess) return e;
-  level_info_kernel<<<1, 1, 0, st>>>(w.ls, nJ, w.info);
+  level_info_kernel<<<nb, 1, 0, st>>>(w.ls, nJ, w.info, bs);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // 2. Ogita-Aishima refinement of the leading nJ eigenpairs
   for (int it = 0; it < refine_steps; ++it) {
     // W = H X_J ; S = X^T W ; XtX = X^T X_J
-    if ((e = dgemm<false>(n, nJ, n, 1.0, w.H, n, w.X, n, 0.0, nullptr, n, w.W, n, st))) return e;
-    if ((e = dgemm<true>(n, nJ, n, 1.0, w.X, n, w.W, n, 0.0, nullptr, n, w.S, n, st))) return e;
-    if ((e = dgemm<true>(n, nJ, n, 1.0, w.X, n, w.X, n, 0.0, nullptr, n, w.R, n, st))) return e;
-    oa_correct_kernel<<<nJ, 256, 0, st>>>(n, nJ, w.S, w.R, w.lam, 1e-5, lambda_floor(w), w.E,
-                                          w.lamJ, w.info);
+    if ((e = dgemm_w<false>(bs, n, nJ, n, 1.0, w.H, n, w.X, n, 0.0, nullptr, n, w.W, n, st))) return e;
+    if ((e = dgemm_w<true>(bs, n, nJ, n, 1.0, w.X, n, w.W, n, 0.0, nullptr, n, w.S, n, st))) return e;
+    if ((e = dgemm_w<true>(bs, n, nJ, n, 1.0, w.X, n, w.X, n, 0.0, nullptr, n, w.R, n, st))) return e;
+    oa_correct_kernel<<<dim3(nJ, nb), 256, 0, st>>>(n, nJ, w.S, w.R, w.lam, 1e-5, lambda_floor(w),
+                                                    w.E, w.lamJ, w.info, bs);
     if ((e = cudaGetLastError())) return e;
     // X_J <- X_J + X E
-    if ((e = dgemm<false>(n, nJ, n, 1.0, w.X, n, w.E, n, 1.0, w.X, n, w.Xn, n, st))) return e;
+    if ((e = dgemm_w<false>(bs, n, nJ, n, 1.0, w.X, n, w.E, n, 1.0, w.X, n, w.Xn, n, st))) return e;
     const int64_t cnt = (int64_t)n * nJ;
-    copy_cols_kernel<<<(unsigned)ceil_div(cnt, 256), 256, 0, st>>>(w.Xn, w.X, cnt);
+    copy_cols_kernel<<<dim3((unsigned)ceil_div(cnt, 256), nb), 256, 0, st>>>(w.Xn, w.X, cnt, bs.nn);
     if ((e = cudaGetLastError())) return e;
   }
   // eigenvalues consistent with the final vectors: sigma_j^2 = x_j^T H x_j / x_j^T x_j,
   // so that every new mode P x_j / sigma_j has unit norm
-  if ((e = dgemm<false>(n, nJ, n, 1.0, w.H, n, w.X, n, 0.0, nullptr, n, w.W, n, st))) return e;
-  rayleigh_kernel<<<nJ, 256, 0, st>>>(n, nJ, w.X, w.W, w.lamJ);
+  if ((e = dgemm_w<false>(bs, n, nJ, n, 1.0, w.H, n, w.X, n, 0.0, nullptr, n, w.W, n, st))) return e;
+  rayleigh_kernel<<<dim3(nJ, nb), 256, 0, st>>>(n, nJ, w.X, w.W, w.lamJ, bs);
   if ((e = cudaGetLastError())) return e;
-  finalize_kernel<<<(unsigned)ceil_div(k1 > 0 ? k1 : 1, kFinCols), 256, 0, st>>>(
-      n, nJ, kc, k1, w.X, w.lamJ, D, ff, sqrt(lambda_floor(w)), w.T, nullptr, w.T64, w.Dnew, w.info);
+  finalize_kernel<<<dim3((unsigned)ceil_div(k1 > 0 ? k1 : 1, kFinCols), nb), 256, 0, st>>>(
+      n, nJ, kc, k1, w.X, w.lamJ, D, ff, sqrt(lambda_floor(w)), w.T, nullptr, w.T64, w.Dnew, w.info,
+      bs);
   *launches = nl + 1 + 6 * refine_steps + 3;
   return cudaGetLastError();
 }
 
-cudaError_t dgemm_flag_launch(bool trans_a, int m, int nn, int k, const double* A, int lda,
-                              const double* B, int ldb, double* C, int ldc, const int* flag,
-                              cudaStream_t st) {
-  return trans_a ? dgemm<true>(m, nn, k, 1.0, A, lda, B, ldb, 0.0, nullptr, ldc, C, ldc, st, flag)
-                 : dgemm<false>(m, nn, k, 1.0, A, lda, B, ldb, 0.0, nullptr, ldc, C, ldc, st, flag);
+cudaError_t dgemm_batched_launch(bool trans_a, int m, int nn, int k, double alpha, const double* A,
+                                 int lda, int64_t sA, const double* B, int ldb, int64_t sB,
+                                 double beta, const double* Cin, int ldci, int64_t sCin, double* C,
+                                 int ldc, int64_t sC, const LevelState* ls, int64_t sls, int count,
+                                 cudaStream_t st) {
+  return trans_a ? dgemm_b<true>(m, nn, k, alpha, A, lda, sA, B, ldb, sB, beta, Cin, ldci, sCin, C,
+                                 ldc, sC, ls, sls, count, st)
+                 : dgemm_b<false>(m, nn, k, alpha, A, lda, sA, B, ldb, sB, beta, Cin, ldci, sCin, C,
+                                  ldc, sC, ls, sls, count, st);
 }
 
 cudaError_t dgemm_launch(bool trans_a, int m, int nn, int k, double alpha, const double* A, int lda,
                          const double* B, int ldb, double beta, const double* Cin, int ldci,
                          double* C, int ldc, cudaStream_t st) {
-  return trans_a ? dgemm<true>(m, nn, k, alpha, A, lda, B, ldb, beta, Cin, ldci, C, ldc, st)
-                 : dgemm<false>(m, nn, k, alpha, A, lda, B, ldb, beta, Cin, ldci, C, ldc, st);
+  return dgemm_batched_launch(trans_a, m, nn, k, alpha, A, lda, 0, B, ldb, 0, beta, Cin, ldci, 0, C,
+                              ldc, 0, nullptr, 0, 1, st);
 }
 
 cudaError_t cholesky_launch(const double* G, int n, double* R, int* info, cudaStream_t st) {

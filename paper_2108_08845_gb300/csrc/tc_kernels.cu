@@ -93,11 +93,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 // Bounded wait on phase `parity`; on expiry sets *abort and the error word.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort,
-                                          int* err) {
+                                          int* err, long long budget = kWaitCycles) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (*abort) return false;
-    if (clock64() - t0 > kWaitCycles) {
+    if (clock64() - t0 > budget) {
       *abort = 1;
       atomicOr(err, 8);  // err points at the handle's status word
       return false;
@@ -584,6 +584,7 @@ struct UpdGeom {
   int nkb;          // K blocks of 64 panel columns: ceil(np / 64)
   int64_t ntiles;   // row tiles of 128
   int Kp;           // column stride of the tiled mode planes
+  long long wait;   // clock-cycle budget of the pipeline waits (drains keep kWaitCycles)
 };
 
 // T3 (N x npk row-major BF16, npk = 64 * nkb): row part*k1p + j, column = padded
@@ -664,7 +665,8 @@ __global__ void __launch_bounds__(192, 1) tc_update_kernel(const __grid_constant
       int stage = 0, issued = 0;
       uint32_t phase = 0;
       for (int64_t t = blockIdx.x; t < u.ntiles && !*abort_flag; t += gridDim.x) {
-        if (issued >= kUpdStages && !mbar_wait(&empty[stage], phase ^ 1, abort_flag, err)) break;
+        if (issued >= kUpdStages && !mbar_wait(&empty[stage], phase ^ 1, abort_flag, err, u.wait))
+          break;
         uint8_t* dst = stages + (size_t)stage * stage_bytes;
         mbar_expect_tx(&full[stage], tx_bytes);
         for (int h = 0; h < 2; ++h) {
@@ -701,7 +703,7 @@ __global__ void __launch_bounds__(192, 1) tc_update_kernel(const __grid_constant
     if (lane == 0) {
       // --------------------------------------------------------- MMA issuer
       const uint32_t idesc = idesc_bf16(u.N, 1, 0);  // A MN-major (rows contiguous), B K-major
-      bool ok = mbar_wait(t_full, 0, abort_flag, err);
+      bool ok = mbar_wait(t_full, 0, abort_flag, err, u.wait);
       tc_fence_after();
       const uint32_t tbase = smem_u32(tsm);
       int stage = 0;
@@ -710,8 +712,8 @@ __global__ void __launch_bounds__(192, 1) tc_update_kernel(const __grid_constant
       for (int64_t t = blockIdx.x; ok && t < u.ntiles; t += gridDim.x, ++it) {
         const int buf = (int)(it & 1);
         const uint32_t use = (uint32_t)((it >> 1) & 1);
-        if (it >= 2 && !mbar_wait(&acc_empty[buf], use ^ 1, abort_flag, err)) break;
-        if (!mbar_wait(&full[stage], phase, abort_flag, err)) break;
+        if (it >= 2 && !mbar_wait(&acc_empty[buf], use ^ 1, abort_flag, err, u.wait)) break;
+        if (!mbar_wait(&full[stage], phase, abort_flag, err, u.wait)) break;
         tc_fence_after();
         const uint32_t abase = smem_u32(stages + (size_t)stage * stage_bytes);
         const uint32_t d_tmem = tmem_base + (uint32_t)(buf * 256);
@@ -741,7 +743,7 @@ __global__ void __launch_bounds__(192, 1) tc_update_kernel(const __grid_constant
     for (int64_t t = blockIdx.x; t < u.ntiles; t += gridDim.x, ++it) {
       const int buf = (int)(it & 1);
       const uint32_t use = (uint32_t)((it >> 1) & 1);
-      if (!mbar_wait(&acc_full[buf], use, abort_flag, err)) break;
+      if (!mbar_wait(&acc_full[buf], use, abort_flag, err, u.wait)) break;
       tc_fence_after();
       const int64_t row = t * kUpdRows + sub * 32 + lane;
       const uint32_t tl = tmem_base + ((uint32_t)(sub * 32) << 16) + (uint32_t)(buf * 256);
@@ -886,6 +888,15 @@ int gram_max_clusters(int npair, int num_sms) {
 
 }  // namespace
 
+// Pipeline-wait budget of tc_update_kernel (psvd_debug_set_wait_budget; 0 = default).
+long long g_update_wait = 0;
+
+int tc_set_wait_budget(int kernel, long long cycles) {
+  if (kernel != 1 || cycles < 0) return PSVD_ERR_INVALID_ARG;
+  g_update_wait = cycles;
+  return PSVD_OK;
+}
+
 size_t tc_t3_elems(int K, int maxB) {
   const int k1p = (K + 15) & ~15;
   const int np = (2 * ((K + 7) & ~7) + ((maxB + 7) & ~7) + 15) & ~15;
@@ -995,6 +1006,7 @@ int tc_update(const __nv_bfloat16* Ut, int Kp, int kc, const void* A, int64_t ld
   u.nkb = (int)ceil_div(u.np, 64);
   u.ntiles = ceil_div(M, kUpdRows);
   u.Kp = Kp;
+  u.wait = g_update_wait > 0 ? g_update_wait : kWaitCycles;
   if (u.np > 256 || u.N > 256 || M > 0x7fffffffll) return PSVD_ERR_SHAPE;
   const int npk = u.nkb * 64;
   const int64_t tcount = (int64_t)u.N * npk;

@@ -33,6 +33,9 @@ size_t tc_t3_elems(int K, int maxB);
 int tc_update(const __nv_bfloat16* Ut, int Kp, int kc, const void* A, int64_t lda, int B, int dtype,
               int64_t M, const float* T, int n, int k1, __nv_bfloat16* T3, __nv_bfloat16* Ut_new,
               int num_sms, int* status, cudaStream_t st);
+// Testing hook of the device-side failure detection: the clock-cycle budget of the
+// pipeline waits of tc_update_kernel (kernel = 1) for later launches; 0 = default.
+int tc_set_wait_budget(int kernel, long long cycles);
 // out = float(Uh) + float(Ul) (exact), M x k column-major with leading dimension ldo.
 cudaError_t tc_modes_to_f32(const __nv_bfloat16* Ut, int Kp, int64_t M, int k, float* out,
                             int64_t ldo, cudaStream_t st);

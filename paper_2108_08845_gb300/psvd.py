@@ -92,6 +92,7 @@ def load(build_if_missing: bool = True):
         lib.psvd_status_string.argtypes = [C.c_int]
         lib.psvd_status_string.restype = C.c_char_p
         lib.psvd_last_info.argtypes = [vp, C.POINTER(C.c_int32)]
+        lib.psvd_debug_set_wait_budget.argtypes = [i32, i64]
         lib.psvd_parallel_qr_static.argtypes = [vp, i64, i64, i32, i32, vp, vp]
         lib.psvd_update_adjoint.argtypes = [vp, i32, vp, i64, vp, vp, i64, i32, i32, i32, vp, i64,
                                             vp, vp, i64, vp, vp, i64, vp, vp, i64]
@@ -315,6 +316,16 @@ def psvd_last_info(h: int):
     info = (C.c_int32 * 4)()
     rc = _check(load().psvd_last_info(h, info), "psvd_last_info")
     return rc, [int(x) for x in info]
+
+
+PSVD_DEBUG_UPDATE_KERNEL = 1
+
+
+def psvd_debug_set_wait_budget(kernel: int, cycles: int) -> int:
+    """Testing hook: clock-cycle budget of the tensor-core update kernel's pipeline
+    waits for later launches (0 restores the default); see include/psvd.h."""
+    return _check(load().psvd_debug_set_wait_budget(int(kernel), int(cycles)),
+                  "psvd_debug_set_wait_budget")
 
 
 def psvd_set_profiling(h: int, enable: bool) -> int:

@@ -59,3 +59,10 @@ def test_new_entry_points_reject_bad_arguments_without_gpu():
     assert lib.psvd_group_stats(None, None, None) == psvd.PSVD_ERR_INVALID_ARG
     lib.psvd_group_destroy(None)  # a null group is ignored
     assert psvd.status_string(psvd.PSVD_WARN_DEGENERATE).startswith("warning: coincident")
+
+
+def test_wait_budget_hook_checks_arguments_without_gpu():
+    lib = psvd.load()
+    assert lib.psvd_debug_set_wait_budget(2, 100) == psvd.PSVD_ERR_INVALID_ARG
+    assert lib.psvd_debug_set_wait_budget(1, -1) == psvd.PSVD_ERR_INVALID_ARG
+    assert lib.psvd_debug_set_wait_budget(1, 0) == psvd.PSVD_OK

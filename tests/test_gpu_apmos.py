@@ -175,3 +175,21 @@ def test_apmos_low_rank_svd_of_w_matches_oracle(p, q):
         # an approximation: the exact APMOS differs beyond rounding
         Le = oracle.apmos(A.double().numpy(), off, r1, r2)[1]
         assert np.abs(Lo / Le - 1).max() > 1e-5
+
+
+def test_apmos_batching_workload_64_partitions():
+    # the batching workload at its full size: 64 row partitions of uniformly drawn
+    # 16,384 - 262,144 rows (about 8.7 M rows in all), N = 64 snapshots, r1 = r2 = 20.
+    # A graded spectrum s_i = 0.85^i over 60 modes plus 1e-5 noise puts every local
+    # truncation at sigma_20 / sigma_1 ~ 0.04 (see test_apmos_uneven_partitions)
+    sizes = synthetic.partition_sizes(64, 16384, 262144, seed=1239)
+    off = _offsets(sizes)
+    Mtot = int(off[-1])
+    A64, _, _, _ = synthetic.low_rank(Mtot, 64, 60, 1e-5, seed=1239,
+                                      s=[0.85 ** i for i in range(60)])
+    A = synthetic.to_storage(A64, torch.float32)
+    del A64
+    U, L, rc = _gpu_apmos(A, off, 20, 20)
+    assert rc == psvd.PSVD_OK
+    Uo, Lo = oracle.apmos(A.double().numpy(), off, 20, 20)
+    _compare(U, L, Uo, Lo, k=16)
