@@ -35,6 +35,9 @@ struct PanelF32 {
   int a_bf16;  // 1: A is bfloat16, 0: float
   int64_t M;
   int n;  // kc + B
+  // set by the Gram launchers: 1 when a BF16 A cannot be read as 4-byte row pairs
+  // (odd leading dimension or base), so its rows are loaded one at a time
+  int a_pairs_unaligned = 0;
 };
 
 // Number of row chunks and partial-buffer doubles used by gram_simt for a panel,

@@ -171,6 +171,17 @@ def test_bf16_inputs_on_fp32_path():
     _compare(U, D, Uo, Do, s_next=s_next)
 
 
+@pytest.mark.parametrize("M", [5000, 3001])
+def test_bf16_odd_and_even_leading_dimension(M):
+    # BF16 snapshots on the FP32 path: an even leading dimension is read as 4-byte row
+    # pairs, an odd one (M = 3001, unpadded) one row at a time; both match the oracle
+    A, _, _, _ = synthetic.low_rank(M, 60, 30, 1e-6, seed=M)
+    bs = [synthetic.to_storage(b, torch.bfloat16) for b in _batches(A, 20)]
+    U, D, _ = _gpu_run(bs, K=8, ff=1.0)
+    Uo, Do, s_next = _oracle_run_gap(bs, 8, 1.0)
+    _compare(U, D, Uo, Do, s_next=s_next)
+
+
 def test_host_and_device_inputs_identical():
     A, _, _, _ = synthetic.low_rank(3000, 60, 20, 1e-6, seed=5)
     bs = [synthetic.to_storage(b, torch.float32) for b in _batches(A, 20)]
