@@ -31,14 +31,19 @@ namespace {
 constexpr int kMaxBatch = 128;
 
 // WW = sum_b Vs_b Vs_b^T, blocks in order, with Vs_b = T64_b[:, 0:r1] diag(sigma_b^2)
-// (T64_b: N x r1 FP64 at T64 + b * N * r1, sigma_b at sigma + b * r1).
+// (T64_b: N x r1 FP64 at T64 + b * N * r1, sigma_b at sigma + b * r1).  The blocks
+// are split into gridDim.y consecutive groups, each summed by its own thread into a
+// partial (part + y N^2); wwt_sum_kernel adds the partials in group order, so every
+// entry is summed in block order as one chain of partial sums.
 __global__ void wwt_kernel(int N, int r1, int nparts, const double* __restrict__ T64,
-                           const double* __restrict__ sigma, double* __restrict__ WW) {
+                           const double* __restrict__ sigma, double* __restrict__ part) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= N * N) return;
   const int i = e % N, j = e / N;
+  const int per = (nparts + gridDim.y - 1) / gridDim.y;
+  const int b0 = blockIdx.y * per, b1 = min(nparts, b0 + per);
   double acc = 0.0;
-  for (int b = 0; b < nparts; ++b) {
+  for (int b = b0; b < b1; ++b) {
     const double* Tb = T64 + (size_t)b * N * r1;
     const double* sb = sigma + (size_t)b * r1;
     for (int k = 0; k < r1; ++k) {
@@ -46,8 +51,20 @@ __global__ void wwt_kernel(int N, int r1, int nparts, const double* __restrict__
       acc = fma(Tb[i + (int64_t)k * N] * s2, Tb[j + (int64_t)k * N] * s2, acc);
     }
   }
-  WW[e] = acc;
+  part[(int64_t)blockIdx.y * N * N + e] = acc;
 }
+
+__global__ void wwt_sum_kernel(int N, int ngroups, const double* __restrict__ part,
+                               double* __restrict__ WW) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N * N) return;
+  double s = 0.0;
+  for (int g = 0; g < ngroups; ++g) s += part[(int64_t)g * N * N + e];
+  WW[e] = s;
+}
+
+// Groups of blocks of the W W^T sum (a few blocks per thread).
+inline int wwt_groups(int nparts) { return nparts < 32 ? nparts : 32; }
 
 // The gathered W (N x m, m = r1 nparts): column (b, k) = +-V_b[:, k] s_bk =
 // +-T64_b[:, k] s_bk^2, signed so that its entries sum to >= 0.  One warp per column.
@@ -118,7 +135,7 @@ struct ApmosCache {
   std::vector<int64_t> items_key;
   int nitems = 0;
   std::vector<int> first_host;
-  Grow<double> T64_all, S_all, WW;
+  Grow<double> T64_all, S_all, WW, WWp;  // WWp: partials of W W^T
   // the randomized global SVD (low_rank): explicit W, X diag(1/s), RandWork arrays
   Grow<double> Wexp, Tout, rB0, rB1, rB2, rMm, rRr, rAw, rBb;
   Grow<float> rOm;
@@ -208,8 +225,12 @@ int apmos_enqueue(ApmosCache* c, const void* A, int64_t lda, int a_bf16, int64_t
     merge_info_kernel<<<1, 1, 0, st>>>(c->info.p, cnt, c->info.p);
     ACK(cudaGetLastError());
   }
-  // W W^T in block order
-  wwt_kernel<<<(unsigned)ceil_div(nn, 256), 256, 0, st>>>(N, r1, nparts, T64_all, S_all, WW);
+  // W W^T in block order (partials of groups of blocks, then their ordered sum)
+  const int ng = wwt_groups(nparts);
+  wwt_kernel<<<dim3((unsigned)ceil_div(nn, 128), (unsigned)ng), 128, 0, st>>>(N, r1, nparts, T64_all,
+                                                                              S_all, c->WWp.p);
+  ACK(cudaGetLastError());
+  wwt_sum_kernel<<<(unsigned)ceil_div(nn, 256), 256, 0, st>>>(N, ng, c->WWp.p, WW);
   ACK(cudaGetLastError());
   // the global solve on problem 0's workspace (its status words collect every block's)
   SmallWork w = batch_work(c, N, 0, 1, c->Tg64.p, 0, c->Dg.p, 0);
@@ -273,7 +294,7 @@ int apmos_run(const void* A, int64_t lda, int a_bf16, int64_t Mtot, const int64_
   if (cudaStreamSynchronize(st) != cudaSuccess) return PSVD_ERR_CUDA;
   const size_t fsz = eig_levels_scratch_floats(N);
   bool ok = c->T64_all.ensure((size_t)nparts * N * r1) && c->S_all.ensure((size_t)nparts * r1) &&
-            c->WW.ensure(nn) && c->H.ensure(nb * nn) && c->X.ensure(nb * nn) &&
+            c->WW.ensure(nn) && c->WWp.ensure(nn * (size_t)wwt_groups(nparts)) && c->H.ensure(nb * nn) && c->X.ensure(nb * nn) &&
             c->lam.ensure((size_t)nb * N) && c->W.ensure(nb * nn) && c->S.ensure(nb * nn) &&
             c->R.ensure(nb * nn) && c->E.ensure(nb * nn) && c->Xn.ensure(nb * nn) &&
             c->lamJ.ensure((size_t)nb * N) && c->T.ensure(nb * nn) && c->Tg64.ensure(nn) &&
@@ -318,7 +339,8 @@ int apmos_run(const void* A, int64_t lda, int a_bf16, int64_t Mtot, const int64_
                               (int64_t)(uintptr_t)U, ldu, (int64_t)(uintptr_t)L, num_sms,
                               (int64_t)(uintptr_t)st, c->nitems};
   for (const void* ptr : {(const void*)c->info.p, (const void*)c->T64_all.p, (const void*)c->S_all.p,
-                          (const void*)c->WW.p, (const void*)c->H.p, (const void*)c->X.p,
+                          (const void*)c->WW.p, (const void*)c->WWp.p, (const void*)c->H.p,
+                          (const void*)c->X.p,
                           (const void*)c->lam.p, (const void*)c->W.p, (const void*)c->S.p,
                           (const void*)c->R.p, (const void*)c->E.p, (const void*)c->Xn.p,
                           (const void*)c->lamJ.p, (const void*)c->T.p, (const void*)c->Tg64.p,

@@ -250,9 +250,12 @@ int step(psvd_ctx* h, const void* A, int64_t lda, int B, int dtype) {
     // an FP64 Gram resolves eigenvalues down to ~1e-13 lambda_max: up to six
     // levels of three decades each reach them.  The refinement converges
     // quadratically from the levels' ~u32/tau accuracy: two steps reach FP64
-    // rounding for the FP32 and tensor-core Grams, the FP64 path takes three
-    CK(small_solve_launch(w, n, kc, k1, Dcur, h->cfg.ff, use_f64(h) ? 3 : 2,
-                          use_f64(h) ? 6 : kMaxLevels, h->st, &nl));
+    // rounding for the FP32 Gram (resolved to ~1e-10 lambda_max), the FP64 path
+    // takes three, and one already lies below the tensor-core Gram's own error
+    // (~1e-9 lambda_max, from its FP32 accumulation chains)
+    const int refine = use_f64(h) ? 3 : use_tc(h) ? 1 : 2;
+    CK(small_solve_launch(w, n, kc, k1, Dcur, h->cfg.ff, refine, use_f64(h) ? 6 : kMaxLevels,
+                          h->st, &nl));
   }
   prof_end(h, pr);
   h->launches += nl;
