@@ -135,6 +135,24 @@ int psvd_initialize(psvd_handle h, const void* A0, int64_t lda, int32_t B, int32
  * its Gram [U|A]^T[U|A] is scaled by diag(ff*D, 1) on the small side. */
 int psvd_incorporate_data(psvd_handle h, const void* A, int64_t lda, int32_t B, int32_t dtype);
 
+/* psvd_incorporate_batches: psvd_incorporate_data on `count` batches in order,
+ * A[0], ..., A[count-1] (host array of pointers; each batch M x B with leading
+ * dimension lda and the given dtype, device or host memory), with the same result
+ * as the count single calls.  Host batches are copied to the device on a copy
+ * stream of the handle into two alternating staging buffers, so the copy of batch
+ * i+1 runs while batch i is processed (pinned host memory makes the copies
+ * asynchronous; pageable memory still works, with less overlap).  s_out (may be
+ * null; host or device, FP64, count x K with leading dimension K) receives each
+ * batch's singular values (the current mode count of them, descending) as soon as
+ * that batch is done.  Returns after enqueuing; the caller keeps every batch and
+ * s_out valid until the handle's stream has finished (psvd_get_* or a stream
+ * synchronisation).  Every batch is checked before the first is enqueued, so an
+ * argument or shape error (as for psvd_incorporate_data) leaves the handle
+ * unchanged; a CUDA error part-way leaves the batches before it applied.  A
+ * pageable host s_out makes each read synchronous, which stalls the pipeline. */
+int psvd_incorporate_batches(psvd_handle h, const void* const* A, int32_t count, int64_t lda,
+                             int32_t B, int32_t dtype, double* s_out);
+
 /* psvd_parallel_qr: the R factor of the row-partitioned QR of Sec. 4.2 for a
  * tall panel P (M x n, ldp >= M, n <= K + max_batch, dtype F32 or BF16), with
  * the handle's M.  R (n x n, upper triangular, diag >= 0) is written to R_out

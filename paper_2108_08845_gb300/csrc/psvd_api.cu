@@ -51,6 +51,13 @@ struct psvd_ctx {
   void* staging = nullptr;
   size_t staging_bytes = 0;
   float* Uf32_tmp = nullptr;  // FP32 view of hi/lo modes for get_modes / save
+  // psvd_incorporate_batches: host batches are copied on their own stream into two
+  // alternating staging buffers while the previous batch is processed
+  cudaStream_t copy_st = nullptr;
+  void* hstg[2] = {nullptr, nullptr};
+  size_t hstg_bytes = 0;
+  cudaEvent_t copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
+  bool hstg_used[2] = {false, false};
   ApmosCache* apmos = nullptr;  // psvd_parallel_svd workspaces and streams (lazily made)
   AdjWork* adj = nullptr;       // psvd_update_adjoint workspaces (lazily made)
   SimtTune tune;                // FP32-path tile choices (psvd_autotune)
@@ -502,6 +509,15 @@ void psvd_destroy(psvd_handle h) {
   cudaFree(h->rw.sgn);
   cudaFree(h->staging);
   cudaFree(h->Uf32_tmp);
+  for (int j = 0; j < 2; ++j) {
+    cudaFree(h->hstg[j]);
+    if (h->copied[j]) cudaEventDestroy(h->copied[j]);
+    if (h->consumed[j]) cudaEventDestroy(h->consumed[j]);
+  }
+  if (h->copy_st) {
+    cudaStreamSynchronize(h->copy_st);
+    cudaStreamDestroy(h->copy_st);
+  }
   apmos_cache_destroy(h->apmos);
   adj_work_destroy(h->adj);
   cudaFree(h->w.T64);
@@ -530,6 +546,80 @@ int psvd_incorporate_data(psvd_handle h, const void* A, int64_t lda, int32_t B, 
   int64_t ldd;
   if (int rc = stage_input(h, A, lda, h->M, B, dtype, use_tc(h), &Ad, &ldd)) return rc;
   return step(h, Ad, ldd, B, dtype);
+}
+
+int psvd_incorporate_batches(psvd_handle h, const void* const* A, int32_t count, int64_t lda,
+                             int32_t B, int32_t dtype, double* s_out) {
+  if (!h || !A || count < 1) return PSVD_ERR_INVALID_ARG;
+  if (h->kc == 0) return PSVD_ERR_NOT_INITIALIZED;
+  // every batch is checked before the first one is enqueued
+  for (int i = 0; i < count; ++i)
+    if (int rc = check_batch(h, A[i], lda, B, dtype)) return rc;
+  const size_t es = (size_t)elem_size(dtype);
+  // staging of host batches: the tensor-core path wants 16-byte aligned columns
+  const int64_t ldst = use_tc(h) ? ceil_div(h->M, 8) * 8 : h->M;
+  const size_t need = es * (size_t)ldst * (size_t)B;
+  bool any_host = false;
+  for (int i = 0; i < count && !any_host; ++i) any_host = !is_device_ptr(A[i]);
+  if (any_host) {
+    if (!h->copy_st) {
+      if (cudaStreamCreateWithFlags(&h->copy_st, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        h->copy_st = nullptr;
+        return PSVD_ERR_CUDA;
+      }
+      for (int j = 0; j < 2; ++j)
+        if (cudaEventCreateWithFlags(&h->copied[j], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->consumed[j], cudaEventDisableTiming) != cudaSuccess) {
+          cudaGetLastError();
+          return PSVD_ERR_CUDA;
+        }
+    }
+    if (need > h->hstg_bytes) {
+      // a buffer may still feed an earlier call's update, or receive its copy
+      CK(cudaStreamSynchronize(h->copy_st));
+      CK(cudaStreamSynchronize(h->st));
+      for (int j = 0; j < 2; ++j) {
+        cudaFree(h->hstg[j]);
+        h->hstg[j] = nullptr;
+        h->hstg_used[j] = false;
+      }
+      h->hstg_bytes = 0;
+      for (int j = 0; j < 2; ++j)
+        if (cudaMalloc(&h->hstg[j], need) != cudaSuccess) {
+          cudaGetLastError();
+          return PSVD_ERR_ALLOC;
+        }
+      h->hstg_bytes = need;
+    }
+  }
+  for (int i = 0; i < count; ++i) {
+    const void* Ad;
+    int64_t ldd;
+    const int j = i & 1;
+    const bool host = any_host && !is_device_ptr(A[i]);
+    if (host) {
+      // staging j is free once the update that read it (two batches back) is done
+      if (h->hstg_used[j]) CK(cudaStreamWaitEvent(h->copy_st, h->consumed[j], 0));
+      CK(cudaMemcpy2DAsync(h->hstg[j], es * ldst, A[i], es * lda, es * h->M, B,
+                           cudaMemcpyHostToDevice, h->copy_st));
+      CK(cudaEventRecord(h->copied[j], h->copy_st));
+      CK(cudaStreamWaitEvent(h->st, h->copied[j], 0));
+      Ad = h->hstg[j];
+      ldd = ldst;
+    } else if (int rc = stage_input(h, A[i], lda, h->M, B, dtype, use_tc(h), &Ad, &ldd)) {
+      return rc;
+    }
+    if (int rc = step(h, Ad, ldd, B, dtype)) return rc;
+    if (host) {
+      CK(cudaEventRecord(h->consumed[j], h->st));
+      h->hstg_used[j] = true;
+    }
+    if (s_out)
+      CK(cudaMemcpyAsync(s_out + (int64_t)i * h->K, h->D[h->cur], sizeof(double) * h->kc,
+                         cudaMemcpyDefault, h->st));
+  }
+  return PSVD_OK;
 }
 
 int psvd_num_modes(psvd_handle h) { return h ? h->kc : PSVD_ERR_INVALID_ARG; }

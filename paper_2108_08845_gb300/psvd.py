@@ -79,6 +79,7 @@ def load(build_if_missing: bool = True):
         lib.psvd_destroy.restype = None
         lib.psvd_initialize.argtypes = [vp, vp, i64, i32, i32]
         lib.psvd_incorporate_data.argtypes = [vp, vp, i64, i32, i32]
+        lib.psvd_incorporate_batches.argtypes = [vp, C.POINTER(vp), i32, i64, i32, i32, vp]
         lib.psvd_parallel_qr.argtypes = [vp, vp, i64, i32, i32, vp]
         lib.psvd_parallel_svd.argtypes = [vp, vp, i64, C.POINTER(C.c_int64), i32, i32, i32, i32,
                                           i32, fp, i64, vp]
@@ -194,6 +195,31 @@ def psvd_initialize(h: int, A0) -> int:
 def psvd_incorporate_data(h: int, A) -> int:
     p, ld, _, B, code, _keep = _mat(A, "A", allow_f64=True)
     return _check(load().psvd_incorporate_data(h, p, ld, B, code), "psvd_incorporate_data")
+
+
+def psvd_incorporate_batches(h: int, batches, s_out=None, K=None) -> int:
+    """psvd_incorporate_data on every batch in order: host batches are copied to the
+    device while the previous batch is processed.  All batches share lda, B and dtype.
+    s_out (optional): contiguous float64, count x K (the handle's K; its size is
+    checked when K is given); row i receives batch i's singular values.  Returns
+    after enqueuing."""
+    ptrs, ld, B, code, _keep = _batch_list(batches, "batches")
+    sp = None
+    if s_out is not None:
+        if hasattr(s_out, "data_ptr"):
+            import torch
+            if s_out.dtype != torch.float64 or not s_out.is_contiguous():
+                raise ValueError("s_out: expected a contiguous float64 tensor")
+            sp, n = s_out.data_ptr(), s_out.numel()
+        else:
+            a = np.asarray(s_out)
+            if a.dtype != np.float64 or not a.flags.c_contiguous:
+                raise ValueError("s_out: expected a contiguous float64 array")
+            sp, n = a.ctypes.data, a.size
+        if K is not None and n < len(ptrs) * K:
+            raise ValueError(f"s_out: needs {len(ptrs)} x {K} elements")
+    return _check(load().psvd_incorporate_batches(h, ptrs, len(ptrs), ld, B, code, sp),
+                  "psvd_incorporate_batches")
 
 
 def psvd_parallel_qr(h: int, P, R_out) -> int:
@@ -411,6 +437,9 @@ class StreamingSVD:
 
     def incorporate_data(self, A):
         return psvd_incorporate_data(self.h, A)
+
+    def incorporate_batches(self, batches, s_out=None):
+        return psvd_incorporate_batches(self.h, batches, s_out, self.K)
 
     @property
     def num_modes(self) -> int:

@@ -53,3 +53,15 @@ def test_adjoint_binding_checks_dtypes_before_calling():
 def test_streaming_svd_needs_cuda_tensors():
     with pytest.raises(ValueError, match="CUDA"):
         streaming_svd([torch.zeros(2, 16).T.requires_grad_(True)], 1, 1.0)
+
+
+def test_incorporate_batches_checks_before_calling():
+    a = torch.zeros(4, 8).T
+    with pytest.raises(ValueError, match="same lda, B and dtype"):
+        psvd.psvd_incorporate_batches(0, [a, torch.zeros(3, 8).T])
+    with pytest.raises(ValueError, match="no batches"):
+        psvd.psvd_incorporate_batches(0, [])
+    with pytest.raises(ValueError, match="float64"):
+        psvd.psvd_incorporate_batches(0, [a], torch.zeros(2, 4, dtype=torch.float32))
+    with pytest.raises(ValueError, match="2 x 4 elements"):
+        psvd.psvd_incorporate_batches(0, [a, a], torch.zeros(1, 4, dtype=torch.float64), K=4)

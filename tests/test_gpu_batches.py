@@ -1,0 +1,73 @@
+"""psvd_incorporate_batches: several batches in one call, host batches copied on a
+copy stream while the previous batch is processed.  The result must be the one of
+the single calls, bit for bit (the same kernels on the same values), for host and
+device batches on the FP32 and tensor-core paths, and each batch's singular values
+must land in s_out."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2108_08845_gb300 import psvd, synthetic
+from tests.test_gpu_fp32 import _compare, _oracle_run_gap
+
+pytestmark = pytest.mark.gpu
+
+
+def _run_single(bs, K, ff, prec):
+    s = psvd.StreamingSVD(bs[0].shape[0], K, bs[0].shape[1], ff, prec)
+    sig = []
+    try:
+        s.initialize(bs[0].cuda())
+        for b in bs[1:]:
+            s.incorporate_data(b.cuda())
+            sig.append(s.singular_values().cpu().numpy())
+        return s.modes().cpu().numpy(), s.singular_values().cpu().numpy(), sig
+    finally:
+        s.close()
+
+
+def _run_batched(bs, K, ff, prec, host):
+    M, B = bs[0].shape
+    s = psvd.StreamingSVD(M, K, B, ff, prec)
+    try:
+        s.initialize(bs[0].cuda())
+        rest = [b.pin_memory() if host else b.cuda() for b in bs[1:]]
+        s_out = torch.zeros((len(rest), K), dtype=torch.float64).pin_memory()
+        s.incorporate_batches(rest, s_out)
+        U, D = s.modes().cpu().numpy(), s.singular_values().cpu().numpy()
+        return U, D, s_out.numpy()
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("prec,dt", [(psvd.PSVD_PREC_FP32, torch.float32),
+                                     (psvd.PSVD_PREC_BF16_TC, torch.bfloat16)])
+@pytest.mark.parametrize("host", [True, False])
+def test_batches_equal_single_calls(prec, dt, host):
+    gen = synthetic.TravellingWaves(96, 128, 64, 1.5, 1e-3, seed=71)
+    bs = [synthetic.to_storage(gen.batch(i, 48), dt) for i in range(6)]
+    U1, D1, sig1 = _run_single(bs, 24, 0.95, prec)
+    U2, D2, sig2 = _run_batched(bs, 24, 0.95, prec, host)
+    assert np.array_equal(U1, U2) and np.array_equal(D1, D2)
+    for i, s in enumerate(sig1):
+        assert np.array_equal(sig2[i, :len(s)], s)
+    # and against the oracle
+    Uo, Do, s_next = _oracle_run_gap(bs, 24, 0.95)
+    unit = 2.0 ** -17 if prec == psvd.PSVD_PREC_BF16_TC else 2.0 ** -24
+    sig_tol, ang_tol = (1e-4, 1e-3) if prec == psvd.PSVD_PREC_BF16_TC else (1e-5, 1e-4)
+    _compare(U2.astype(np.float64), D2, Uo, Do, sig_tol=sig_tol, ang_tol=ang_tol, unit=unit,
+             s_next=s_next)
+
+
+def test_batches_reject_mismatched_shapes():
+    s = psvd.StreamingSVD(4096, 8, 32, 1.0)
+    try:
+        a = torch.randn(4096, 32).T.contiguous().T.cuda()
+        s.initialize(a)
+        with pytest.raises(ValueError):
+            psvd.psvd_incorporate_batches(s.h, [a, a[:, :16]])
+        with pytest.raises(psvd.PsvdError) as e:
+            psvd.psvd_incorporate_batches(s.h, [torch.randn(4096, 40).T.contiguous().T.cuda()])
+        assert e.value.status == psvd.PSVD_ERR_SHAPE
+    finally:
+        s.close()
