@@ -272,18 +272,25 @@ int psvd_update_adjoint(psvd_handle h, int32_t kc, const float* U, int64_t ldu, 
                         float* U_bar, int64_t ld_bar, double* D_bar, float* A_bar,
                         int64_t lda_bar);
 
-/* psvd_autotune: picks the FP32 path's tile shapes for this handle's steady-state
- * panel (M rows, n = K + B columns) by timing the candidates on the handle's stream
- * with a representative batch A (DEVICE pointer, M x B, lda >= M, PSVD_F32 or
- * PSVD_BF16): Gram row chunks sized for 1, 2, 4 or 8 resident CTAs per SM, and
- * mode-update tiles of 64 or 128 rows.  The fastest of each is kept by the handle
- * and cached for the process under (M, n, dtype, SM count), so later calls with the
- * same shape take it without timing.  The choice changes only the summation order
- * of the Gram's row chunks (results stay within the same rounding bounds).
- * choice (may be null) receives {CTAs per SM, update tile rows}.  FP32 handles only
- * (PSVD_ERR_UNSUPPORTED otherwise).  Synchronises; the handle's modes, singular
- * values and status are unchanged.  Call it between updates, not inside a group's
- * steady state (a changed tile re-captures the group's graphs). */
+/* psvd_autotune: picks this handle's launch shapes for its steady-state panel (M
+ * rows, n = K + B columns) by timing the candidates on the handle's stream with a
+ * representative batch A (DEVICE pointer, M x B, lda >= M).  The fastest of each
+ * is kept by the handle and cached for the process under the shape and SM count, so
+ * later calls with the same shape take it without timing.
+ *   FP32 handles (A PSVD_F32 or PSVD_BF16): Gram row chunks sized for 1, 2, 4 or
+ *   8 resident CTAs per SM, and mode-update tiles of 64 or 128 rows; choice
+ *   receives {CTAs per SM, update tile rows, 0}.
+ *   Tensor-core handles (A PSVD_BF16): the Gram's cluster count (the resident
+ *   maximum, 2/3, 1/2 or 1/3 of it), the update's CTA count (one per SM or half
+ *   of that) and its pipeline stages (2 to 4, those that fit in shared memory at
+ *   this panel width); choice receives {Gram clusters, update CTAs, update
+ *   stages}.
+ * The Gram choices change only the summation order of its row partial sums
+ * (results stay within the same rounding bounds); the update choices leave the
+ * results unchanged.  choice may be null, else int32_t[3].  FP64 handles:
+ * PSVD_ERR_UNSUPPORTED.  Synchronises; the handle's modes, singular values and
+ * status are unchanged.  Call it between updates; a group whose member was retuned
+ * captures its graphs again. */
 int psvd_autotune(psvd_handle h, const void* A, int64_t lda, int32_t B, int32_t dtype,
                   int32_t* choice);
 

@@ -61,6 +61,7 @@ struct psvd_ctx {
   ApmosCache* apmos = nullptr;  // psvd_parallel_svd workspaces and streams (lazily made)
   AdjWork* adj = nullptr;       // psvd_update_adjoint workspaces (lazily made)
   SimtTune tune;                // FP32-path tile choices (psvd_autotune)
+  TcTune tctune;                // tensor-core launch shapes (psvd_autotune)
   int host_info[4] = {0, 0, 0, 0};
   int sticky_status = 0;
   // per-phase event timing (psvd_set_profiling)
@@ -206,11 +207,11 @@ int panel_gram(psvd_ctx* h, const void* A, int64_t lda, int B, int dtype, int kc
                const double* D, double* G) {
   const int n = kc + B;
   if (use_tc(h)) {
-    int rc = tc_gram(h->Ut[h->cur], h->Kp, kc, A, lda, B, dtype, h->M, h->num_sms, &h->partial,
-                     &h->partial_cap, &h->w.info[2], h->st);
+    int rc = tc_gram(h->Ut[h->cur], h->Kp, kc, A, lda, B, dtype, h->M, h->num_sms, h->tctune,
+                     &h->partial, &h->partial_cap, &h->w.info[2], h->st);
     if (rc) return rc;
-    return tc_gram_reduce(h->partial, h->M, kc, B, h->num_sms, ff, D, G, h->w.H, &h->w.info[2],
-                          h->st)
+    return tc_gram_reduce(h->partial, h->M, kc, B, h->num_sms, h->tctune, ff, D, G, h->w.H,
+                          &h->w.info[2], h->st)
                ? PSVD_ERR_CUDA
                : PSVD_OK;
   }
@@ -269,7 +270,7 @@ int step(psvd_ctx* h, const void* A, int64_t lda, int B, int dtype) {
   pr = prof_begin(h, 2);
   if (use_tc(h)) {
     int rc = tc_update(h->Ut[h->cur], h->Kp, kc, A, lda, B, dtype, h->M, T, n, k1, w.T3,
-                       h->Ut[h->cur ^ 1], h->num_sms, &h->w.info[2], h->st);
+                       h->Ut[h->cur ^ 1], h->num_sms, h->tctune, &h->w.info[2], h->st);
     if (rc) return rc;
   } else if (use_f64(h)) {
     PanelF64 p{h->U64[h->cur], h->ldu, kc, A, lda, dtype, h->M, n};
@@ -315,6 +316,7 @@ int collect_status(psvd_ctx* h) {
 namespace {
 std::mutex g_tune_mu;
 std::map<std::tuple<int64_t, int, int, int>, SimtTune> g_tune_cache;  // (M, n, dtype, SMs)
+std::map<std::tuple<int64_t, int, int>, TcTune> g_tc_tune_cache;      // (M, n, SMs)
 
 // Mean time of `reps` launches of fn on st (after one warm-up launch), in ms.
 template <typename F>
@@ -839,6 +841,9 @@ int group_step(psvd_group* g, const void* const* A, int64_t lda, int32_t B, int3
     for (size_t i = 0; i < n; ++i) {
       key.push_back((int64_t)(uintptr_t)A[i]);
       key.push_back(g->m[i]->cur);
+      // a member retuned by psvd_autotune launches other shapes: capture again
+      key.push_back(g->m[i]->tune.gram_ctas_per_sm);
+      key.push_back(g->m[i]->tune.update_rows);
     }
   }
   const int parity = n ? g->m[0]->cur : 0;
@@ -996,9 +1001,100 @@ int psvd_group_status(psvd_group_handle g) {
 
 // ---------------------------------------------------------------- autotuner
 
+namespace {
+// psvd_autotune on a tensor-core handle: the Gram's cluster count, then the
+// update's CTA count and stage count, each timed on the steady-state panel.
+int autotune_tc(psvd_handle h, const void* A, int64_t lda, int32_t B, int32_t* choice) {
+  const int n = h->K + B;
+  const auto key = std::make_tuple(h->M, n, h->num_sms);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tc_tune_cache.find(key);
+    if (it != g_tc_tune_cache.end()) {
+      h->tctune = it->second;
+      if (choice) {
+        choice[0] = h->tctune.gram_clusters;
+        choice[1] = h->tctune.upd_ctas;
+        choice[2] = h->tctune.upd_stages;
+      }
+      return PSVD_OK;
+    }
+  }
+  const int max_st = tc_update_max_stages(h->K, B, h->K);
+  if (max_st < 2) return PSVD_ERR_SHAPE;
+  // the trials read the current modes and write only scratch (the other mode
+  // buffer, the Gram partials, w.H, w.T3) and the status word, restored afterwards
+  int saved_info[4];
+  CK(cudaMemcpyAsync(saved_info, h->w.info, sizeof(saved_info), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  const int mx = tc_gram_clusters_max(h->K, B, h->num_sms);
+  TcTune best, trial;
+  float best_ms = 1e30f;
+  const int cands[] = {mx, (2 * mx) / 3, mx / 2, mx / 3};
+  for (int i = 0; i < 4; ++i) {
+    const int c = cands[i];
+    if (c < 1 || (i > 0 && c == cands[i - 1])) continue;
+    trial.gram_clusters = c;
+    float ms = 0.f;
+    int rc = time_ms(h->st, 3, [&]() -> int {
+      int r = tc_gram(h->Ut[h->cur], h->Kp, h->K, A, lda, B, PSVD_BF16, h->M, h->num_sms, trial,
+                      &h->partial, &h->partial_cap, &h->w.info[2], h->st);
+      if (r) return r;
+      return tc_gram_reduce(h->partial, h->M, h->K, B, h->num_sms, trial, 1.0, h->D[h->cur],
+                            nullptr, h->w.H, &h->w.info[2], h->st) == cudaSuccess
+                 ? PSVD_OK
+                 : PSVD_ERR_CUDA;
+    }, &ms);
+    if (rc) return rc;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best.gram_clusters = c;
+    }
+  }
+  best_ms = 1e30f;
+  const int ctas[] = {h->num_sms, h->num_sms / 2};
+  for (int c : ctas) {
+    for (int stg = 2; stg <= (max_st < 4 ? max_st : 4); ++stg) {
+      trial.upd_ctas = c;
+      trial.upd_stages = stg;
+      float ms = 0.f;
+      int rc = time_ms(h->st, 3, [&]() -> int {
+        return tc_update(h->Ut[h->cur], h->Kp, h->K, A, lda, B, PSVD_BF16, h->M, h->w.T, n, h->K,
+                         h->w.T3, h->Ut[h->cur ^ 1], h->num_sms, trial, &h->w.info[2], h->st);
+      }, &ms);
+      if (rc) return rc;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best.upd_ctas = c;
+        best.upd_stages = stg;
+      }
+    }
+  }
+  CK(cudaMemcpyAsync(h->w.info, saved_info, sizeof(saved_info), cudaMemcpyHostToDevice, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  h->tctune = best;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tc_tune_cache[key] = best;
+  }
+  if (choice) {
+    choice[0] = best.gram_clusters;
+    choice[1] = best.upd_ctas;
+    choice[2] = best.upd_stages;
+  }
+  return PSVD_OK;
+}
+}  // namespace
+
 int psvd_autotune(psvd_handle h, const void* A, int64_t lda, int32_t B, int32_t dtype,
                   int32_t* choice) {
   if (!h) return PSVD_ERR_INVALID_ARG;
+  if (h->cfg.precision == PSVD_PREC_BF16_TC) {
+    if (!A || B < 1 || B > h->maxB || lda < h->M || dtype != PSVD_BF16) return PSVD_ERR_INVALID_ARG;
+    if (!is_device_ptr(A)) return PSVD_ERR_INVALID_ARG;
+    if (h->M < (int64_t)h->K + B) return PSVD_ERR_SHAPE;
+    return autotune_tc(h, A, lda, B, choice);
+  }
   if (h->cfg.precision != PSVD_PREC_FP32) return PSVD_ERR_UNSUPPORTED;
   if (!A || B < 1 || B > h->maxB || lda < h->M || (dtype != PSVD_F32 && dtype != PSVD_BF16))
     return PSVD_ERR_INVALID_ARG;
@@ -1014,6 +1110,7 @@ int psvd_autotune(psvd_handle h, const void* A, int64_t lda, int32_t B, int32_t 
       if (choice) {
         choice[0] = h->tune.gram_ctas_per_sm;
         choice[1] = h->tune.update_rows;
+        choice[2] = 0;
       }
       return PSVD_OK;
     }
@@ -1073,6 +1170,7 @@ int psvd_autotune(psvd_handle h, const void* A, int64_t lda, int32_t B, int32_t 
   if (choice) {
     choice[0] = best.gram_ctas_per_sm;
     choice[1] = best.update_rows;
+    choice[2] = 0;
   }
   return PSVD_OK;
 }

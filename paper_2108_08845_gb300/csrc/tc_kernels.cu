@@ -62,7 +62,7 @@ constexpr int kGramEpiWarp0 = 2;
 constexpr int kGramEpiWarps = 16;
 constexpr int kGramThreads = (kGramEpiWarp0 + kGramEpiWarps) * 32;
 constexpr int kUpdRows = 128;             // rows per update tile (UMMA M)
-constexpr int kUpdStages = 2;
+constexpr int kUpdMaxStages = 8;          // bound of the runtime stage count (barrier space)
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
 
 // ------------------------------------------------------------------ PTX helpers
@@ -584,6 +584,7 @@ struct UpdGeom {
   int nkb;          // K blocks of 64 panel columns: ceil(np / 64)
   int64_t ntiles;   // row tiles of 128
   int Kp;           // column stride of the tiled mode planes
+  int stages;       // pipeline stages (2 .. kUpdMaxStages)
   long long wait;   // clock-cycle budget of the pipeline waits (drains keep kWaitCycles)
 };
 
@@ -622,10 +623,10 @@ __global__ void __launch_bounds__(192, 1) tc_update_kernel(const __grid_constant
   const int stage_bytes = 2 * half_bytes;    // 128 rows
   const int tb_bytes = u.N * 128;            // one 64-column K block of T3
   uint8_t* stages = base;
-  uint8_t* tsm = stages + (size_t)kUpdStages * stage_bytes;
+  uint8_t* tsm = stages + (size_t)u.stages * stage_bytes;
   uint64_t* full = (uint64_t*)(tsm + (size_t)u.nkb * tb_bytes);
-  uint64_t* empty = full + kUpdStages;
-  uint64_t* t_full = empty + kUpdStages;
+  uint64_t* empty = full + u.stages;
+  uint64_t* t_full = empty + u.stages;
   uint64_t* acc_full = t_full + 1;   // [2]
   uint64_t* acc_empty = acc_full + 2;  // [2]
   uint64_t* mma_done = acc_empty + 2;
@@ -634,7 +635,7 @@ __global__ void __launch_bounds__(192, 1) tc_update_kernel(const __grid_constant
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kUpdStages; ++s) {
+    for (int s = 0; s < u.stages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -665,7 +666,7 @@ __global__ void __launch_bounds__(192, 1) tc_update_kernel(const __grid_constant
       int stage = 0, issued = 0;
       uint32_t phase = 0;
       for (int64_t t = blockIdx.x; t < u.ntiles && !*abort_flag; t += gridDim.x) {
-        if (issued >= kUpdStages && !mbar_wait(&empty[stage], phase ^ 1, abort_flag, err, u.wait))
+        if (issued >= u.stages && !mbar_wait(&empty[stage], phase ^ 1, abort_flag, err, u.wait))
           break;
         uint8_t* dst = stages + (size_t)stage * stage_bytes;
         mbar_expect_tx(&full[stage], tx_bytes);
@@ -680,15 +681,15 @@ __global__ void __launch_bounds__(192, 1) tc_update_kernel(const __grid_constant
           tma_load_2d(&mA, &full[stage], d + 2 * u.kcp * 128, row, 0);
         }
         ++issued;
-        if (++stage == kUpdStages) {
+        if (++stage == u.stages) {
           stage = 0;
           phase ^= 1;
         }
       }
-      const int inflight = issued < kUpdStages ? issued : kUpdStages;
+      const int inflight = issued < u.stages ? issued : u.stages;
       for (int i = 0; i < inflight; ++i) {
         if (--stage < 0) {
-          stage = kUpdStages - 1;
+          stage = u.stages - 1;
           phase ^= 1;
         }
         const long long t0 = clock64();
@@ -726,7 +727,7 @@ __global__ void __launch_bounds__(192, 1) tc_update_kernel(const __grid_constant
         }
         umma_commit(&empty[stage]);
         umma_commit(&acc_full[buf]);
-        if (++stage == kUpdStages) {
+        if (++stage == u.stages) {
           stage = 0;
           phase ^= 1;
         }
@@ -911,15 +912,27 @@ size_t tc_modes_elems(int64_t M, int K) {
   return (size_t)ceil_div(M, (int64_t)128) * 4 * (size_t)((K + 7) & ~7) * 64;
 }
 
+int tc_gram_clusters_max(int kc, int B, int num_sms) {
+  const int np = 2 * ((kc + 7) & ~7) + ((B + 7) & ~7);
+  return gram_max_clusters(np > kSlab ? 3 : 1, num_sms);
+}
+
+namespace {
+// Clusters of one Gram launch: the tuned count, capped at the resident maximum.
+int gram_clusters(int kc, int B, int num_sms, const TcTune& tune) {
+  const int mx = tc_gram_clusters_max(kc, B, num_sms);
+  return (tune.gram_clusters > 0 && tune.gram_clusters < mx) ? tune.gram_clusters : mx;
+}
+}  // namespace
+
 int tc_gram(const __nv_bfloat16* Ut, int Kp, int kc, const void* A, int64_t lda, int B, int dtype,
-            int64_t M, int num_sms, double** partial, int64_t* partial_cap, int* status,
-            cudaStream_t st) {
+            int64_t M, int num_sms, const TcTune& tune, double** partial, int64_t* partial_cap,
+            int* status, cudaStream_t st) {
   if (dtype != PSVD_BF16) return PSVD_ERR_UNSUPPORTED;
   const int np = 2 * ((kc + 7) & ~7) + ((B + 7) & ~7);
   if (np > 256 || M > 0x7fffffffll - 256) return PSVD_ERR_SHAPE;
-  const int npair = np > kSlab ? 3 : 1;
   if (kc > Kp) return PSVD_ERR_SHAPE;
-  GramGeom g = gram_geom(M, kc, B, gram_max_clusters(npair, num_sms), Kp);
+  GramGeom g = gram_geom(M, kc, B, gram_clusters(kc, B, num_sms, tune), Kp);
   PanelMaps pm;
   const int64_t nlines = ceil_div(M, (int64_t)128) * 4 * Kp;
   for (int wi = 0; wi < 4; ++wi) {
@@ -974,10 +987,10 @@ int tc_gram(const __nv_bfloat16* Ut, int Kp, int kc, const void* A, int64_t lda,
   return PSVD_OK;
 }
 
-cudaError_t tc_gram_reduce(const double* partial, int64_t M, int kc, int B, int num_sms, double ff,
-                           const double* D, double* G, double* H, int* status, cudaStream_t st) {
-  const int np = 2 * ((kc + 7) & ~7) + ((B + 7) & ~7);
-  GramGeom g = gram_geom(M, kc, B, gram_max_clusters(np > kSlab ? 3 : 1, num_sms), 0);
+cudaError_t tc_gram_reduce(const double* partial, int64_t M, int kc, int B, int num_sms,
+                           const TcTune& tune, double ff, const double* D, double* G, double* H,
+                           int* status, cudaStream_t st) {
+  GramGeom g = gram_geom(M, kc, B, gram_clusters(kc, B, num_sms, tune), 0);
   const int64_t per = (int64_t)g.npair * kSlab * kSlab;
   double* Ssum = const_cast<double*>(partial) + g.nrange * per;
   tc_gram_sum_kernel<<<(unsigned)ceil_div(per, 256), 256, 0, st>>>(partial, g.nrange, g.npair, Ssum);
@@ -990,11 +1003,29 @@ cudaError_t tc_gram_reduce(const double* partial, int64_t M, int kc, int B, int 
   return cudaGetLastError();
 }
 
+namespace {
+// Shared memory of the update kernel: stages of 128 panel rows, T3 resident,
+// barriers.
+size_t update_smem(int np, int nkb, int N, int stages) {
+  return 1024 + (size_t)stages * 2 * np * 128 + (size_t)nkb * N * 128 + 256;
+}
+constexpr size_t kMaxDynSmem = 232448;
+}  // namespace
+
+int tc_update_max_stages(int kc, int B, int k1) {
+  const int np = (2 * ((kc + 7) & ~7) + ((B + 7) & ~7) + 15) & ~15;
+  const int N = 3 * ((k1 + 15) & ~15);
+  const int nkb = (int)ceil_div(np, 64);
+  int s = 0;
+  while (s < kUpdMaxStages && update_smem(np, nkb, N, s + 1) <= kMaxDynSmem) ++s;
+  return s >= 2 ? s : 0;
+}
+
 int tc_update(const __nv_bfloat16* Ut, int Kp, int kc, const void* A, int64_t lda, int B, int dtype,
               int64_t M, const float* T, int n, int k1, __nv_bfloat16* T3, __nv_bfloat16* Ut_new,
-              int num_sms, int* status, cudaStream_t st) {
+              int num_sms, const TcTune& tune, int* status, cudaStream_t st) {
   if (dtype != PSVD_BF16) return PSVD_ERR_UNSUPPORTED;
-  UpdGeom u;
+  UpdGeom u{};
   u.M = M;
   u.kcp = (kc + 7) & ~7;
   u.Bp = (B + 7) & ~7;
@@ -1023,11 +1054,15 @@ int tc_update(const __nv_bfloat16* Ut, int Kp, int kc, const void* A, int64_t ld
   }
   // T3 is N rows x npk columns, row-major: a "column-major" npk x N matrix
   if (!make_map(&mT, T3, npk, u.N, npk, u.N)) return PSVD_ERR_INVALID_ARG;
-  const size_t smem = 1024 + (size_t)kUpdStages * 2 * u.np * 128 + (size_t)u.nkb * u.N * 128 + 256;
-  if (smem > 232448) return PSVD_ERR_SHAPE;
+  // the tuned stage count, capped at what fits; two at least
+  const int max_st = tc_update_max_stages(kc, B, k1);
+  if (max_st < 2) return PSVD_ERR_SHAPE;
+  u.stages = tune.upd_stages < 2 ? 2 : (tune.upd_stages > max_st ? max_st : tune.upd_stages);
+  const size_t smem = update_smem(u.np, u.nkb, u.N, u.stages);
   if (cudaFuncSetAttribute(tc_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
     return PSVD_ERR_CUDA;
-  const int grid = (int)(u.ntiles < num_sms ? u.ntiles : num_sms);
+  const int ctas = (tune.upd_ctas > 0 && tune.upd_ctas < num_sms) ? tune.upd_ctas : num_sms;
+  const int grid = (int)(u.ntiles < ctas ? u.ntiles : ctas);
   tc_update_kernel<<<grid, 192, smem, st>>>(mU, mA, mT, u, Ut_new, status);
   return cudaGetLastError() == cudaSuccess ? PSVD_OK : PSVD_ERR_CUDA;
 }

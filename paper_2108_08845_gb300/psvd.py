@@ -330,12 +330,15 @@ def psvd_update_adjoint(h: int, U, D, A, U_new, D_new, U_new_bar, D_new_bar, U_b
 
 
 def psvd_autotune(h: int, A):
-    """Times the FP32 path's tile choices on the representative device batch A and keeps
-    the fastest; returns (Gram CTAs per SM, update tile rows)."""
-    p, ld, _, B, code, _keep = _mat(A, "A")
-    ch = (C.c_int32 * 2)()
+    """Times the handle's launch-shape choices on the representative device batch A and
+    keeps the fastest.  Returns (Gram CTAs per SM, update tile rows) for an FP32 handle,
+    (Gram clusters, update CTAs, update stages) for a tensor-core handle."""
+    p, ld, _, B, code, _keep = _mat(A, "A", allow_f64=True)
+    ch = (C.c_int32 * 3)()
     _check(load().psvd_autotune(h, p, ld, B, code, ch), "psvd_autotune")
-    return int(ch[0]), int(ch[1])
+    if ch[2] == 0:
+        return int(ch[0]), int(ch[1])
+    return int(ch[0]), int(ch[1]), int(ch[2])
 
 
 def psvd_last_info(h: int):
