@@ -58,6 +58,16 @@ struct psvd_ctx {
   size_t hstg_bytes = 0;
   cudaEvent_t copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
   bool hstg_used[2] = {false, false};
+  // psvd_incorporate_batches on the tensor-core path: A^T A of the next device batch
+  // is summed on its own stream while this batch's small solve runs (it needs no
+  // modes), and the next Gram computes only the blocks that involve the modes
+  cudaStream_t aa_st = nullptr;
+  cudaEvent_t aa_go = nullptr, aa_done = nullptr;
+  double* aa_partial = nullptr;
+  int64_t aa_cap = 0;
+  double* aa_sum = nullptr;      // 128 x 128 FP64
+  const void* aa_src = nullptr;  // the batch aa_sum belongs to ...
+  int64_t aa_iter = -1;          // ... and the step that may use it
   ApmosCache* apmos = nullptr;  // psvd_parallel_svd workspaces and streams (lazily made)
   AdjWork* adj = nullptr;       // psvd_update_adjoint workspaces (lazily made)
   SimtTune tune;                // FP32-path tile choices (psvd_autotune)
@@ -207,11 +217,16 @@ int panel_gram(psvd_ctx* h, const void* A, int64_t lda, int B, int dtype, int kc
                const double* D, double* G) {
   const int n = kc + B;
   if (use_tc(h)) {
+    // A^T A already summed for this batch (psvd_incorporate_batches): split Gram
+    const bool split = kc > 0 && h->aa_iter == h->iteration && h->aa_src == A &&
+                       tc_gram_can_split(kc, B);
+    h->aa_iter = -1;
     int rc = tc_gram(h->Ut[h->cur], h->Kp, kc, A, lda, B, dtype, h->M, h->num_sms, h->tctune,
-                     &h->partial, &h->partial_cap, &h->w.info[2], h->st);
+                     split, &h->partial, &h->partial_cap, &h->w.info[2], h->st);
     if (rc) return rc;
-    return tc_gram_reduce(h->partial, h->M, kc, B, h->num_sms, h->tctune, ff, D, G, h->w.H,
-                          &h->w.info[2], h->st)
+    if (split) CK(cudaStreamWaitEvent(h->st, h->aa_done, 0));
+    return tc_gram_reduce(h->partial, h->M, kc, B, h->num_sms, h->tctune,
+                          split ? h->aa_sum : nullptr, ff, D, G, h->w.H, &h->w.info[2], h->st)
                ? PSVD_ERR_CUDA
                : PSVD_OK;
   }
@@ -232,7 +247,11 @@ int panel_gram(psvd_ctx* h, const void* A, int64_t lda, int B, int dtype, int kc
 
 // One application of Algorithm 1's small solve + mode update; kc = 0 is the
 // initialisation I1-I2 (the panel is A0 alone).
-int step(psvd_ctx* h, const void* A, int64_t lda, int B, int dtype) {
+// A_next (may be null): the next batch (device memory, the same B and dtype, leading
+// dimension ld_next, no staging needed), whose A^T A block the tensor-core path sums
+// during this step's small solve.
+int step(psvd_ctx* h, const void* A, int64_t lda, int B, int dtype, const void* A_next = nullptr,
+         int64_t ld_next = 0) {
   const int kc = h->kc;
   const int n = kc + B;
   const int k1 = (h->K < n) ? h->K : n;
@@ -242,6 +261,20 @@ int step(psvd_ctx* h, const void* A, int64_t lda, int B, int dtype) {
   if (int rc = panel_gram(h, A, lda, B, dtype, kc, h->cfg.ff, Dcur, nullptr)) return rc;
   prof_end(h, pr);
   h->launches += use_tc(h) ? 3 : 2;
+  if (A_next && use_tc(h) && tc_gram_can_split(k1, B)) {
+    // on the side stream, after this Gram's blocks are assembled (aa_sum is free),
+    // with SMs left over for the small solve's kernels
+    CK(cudaEventRecord(h->aa_go, h->st));
+    CK(cudaStreamWaitEvent(h->aa_st, h->aa_go, 0));
+    const int ctas = h->num_sms > 32 ? h->num_sms - 16 : h->num_sms / 2;
+    if (int rc = tc_gram_aa(A_next, ld_next, B, h->M, h->num_sms, ctas, &h->aa_partial,
+                            &h->aa_cap, h->aa_sum, &h->w.info[2], h->aa_st))
+      return rc;
+    CK(cudaEventRecord(h->aa_done, h->aa_st));
+    h->aa_src = A_next;
+    h->aa_iter = h->iteration + 1;
+    h->launches += 2;
+  }
   SmallWork w = h->w;
   w.Dnew = Dnext;
   pr = prof_begin(h, 1);
@@ -520,6 +553,14 @@ void psvd_destroy(psvd_handle h) {
     cudaStreamSynchronize(h->copy_st);
     cudaStreamDestroy(h->copy_st);
   }
+  if (h->aa_st) {
+    cudaStreamSynchronize(h->aa_st);
+    cudaStreamDestroy(h->aa_st);
+  }
+  if (h->aa_go) cudaEventDestroy(h->aa_go);
+  if (h->aa_done) cudaEventDestroy(h->aa_done);
+  cudaFree(h->aa_partial);
+  cudaFree(h->aa_sum);
   apmos_cache_destroy(h->apmos);
   adj_work_destroy(h->adj);
   cudaFree(h->w.T64);
@@ -537,6 +578,7 @@ int psvd_initialize(psvd_handle h, const void* A0, int64_t lda, int32_t B, int32
   CK(cudaMemsetAsync(h->w.info, 0, sizeof(int) * 4, h->st));
   h->sticky_status = 0;
   h->iteration = 0;
+  h->aa_iter = -1;
   return step(h, Ad, ldd, B, dtype);
 }
 
@@ -595,6 +637,29 @@ int psvd_incorporate_batches(psvd_handle h, const void* const* A, int32_t count,
       h->hstg_bytes = need;
     }
   }
+  // device batches that need no staging: each step sums the next one's A^T A
+  // during its small solve (tensor-core path)
+  auto direct = [&](const void* p) {
+    return is_device_ptr(p) && ((uintptr_t)p & 15) == 0 && ((size_t)lda * es) % 16 == 0;
+  };
+  bool lookahead = false;
+  if (use_tc(h) && count > 1 && tc_gram_can_split(h->K, B)) {
+    for (int i = 1; i < count && !lookahead; ++i) lookahead = direct(A[i]);
+    if (lookahead && !h->aa_st) {
+      if (cudaStreamCreateWithFlags(&h->aa_st, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&h->aa_go, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&h->aa_done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return PSVD_ERR_CUDA;
+      }
+    }
+    if (lookahead && !h->aa_sum) {
+      if (cudaMalloc(&h->aa_sum, sizeof(double) * 128 * 128) != cudaSuccess) {
+        cudaGetLastError();
+        return PSVD_ERR_ALLOC;
+      }
+    }
+  }
   for (int i = 0; i < count; ++i) {
     const void* Ad;
     int64_t ldd;
@@ -612,7 +677,8 @@ int psvd_incorporate_batches(psvd_handle h, const void* const* A, int32_t count,
     } else if (int rc = stage_input(h, A[i], lda, h->M, B, dtype, use_tc(h), &Ad, &ldd)) {
       return rc;
     }
-    if (int rc = step(h, Ad, ldd, B, dtype)) return rc;
+    const void* nxt = (lookahead && i + 1 < count && direct(A[i + 1])) ? A[i + 1] : nullptr;
+    if (int rc = step(h, Ad, ldd, B, dtype, nxt, lda)) return rc;
     if (host) {
       CK(cudaEventRecord(h->consumed[j], h->st));
       h->hstg_used[j] = true;
@@ -1038,9 +1104,9 @@ int autotune_tc(psvd_handle h, const void* A, int64_t lda, int32_t B, int32_t* c
     float ms = 0.f;
     int rc = time_ms(h->st, 3, [&]() -> int {
       int r = tc_gram(h->Ut[h->cur], h->Kp, h->K, A, lda, B, PSVD_BF16, h->M, h->num_sms, trial,
-                      &h->partial, &h->partial_cap, &h->w.info[2], h->st);
+                      false, &h->partial, &h->partial_cap, &h->w.info[2], h->st);
       if (r) return r;
-      return tc_gram_reduce(h->partial, h->M, h->K, B, h->num_sms, trial, 1.0, h->D[h->cur],
+      return tc_gram_reduce(h->partial, h->M, h->K, B, h->num_sms, trial, nullptr, 1.0, h->D[h->cur],
                             nullptr, h->w.H, &h->w.info[2], h->st) == cudaSuccess
                  ? PSVD_OK
                  : PSVD_ERR_CUDA;

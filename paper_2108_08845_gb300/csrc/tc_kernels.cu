@@ -257,6 +257,7 @@ struct GramGeom {
   int64_t nslot;       // 128-row slots covering M
   int64_t nrange;      // clusters; cluster r takes slots r, r + nrange, ...
   int fold_stages;     // 64-row stages (4 MMAs each) per FP32 accumulation chain
+  int split;           // 1: blocks (0,0) and (0,1) only, slab 0 = [Uh | Ul], slab 1 = A
 };
 
 // Tensor maps of the three panel planes (Uh, Ul, A) with boxes of 64 rows x
@@ -398,6 +399,13 @@ __global__ void __launch_bounds__(kGramThreads, 1) tc_gram_kernel(const __grid_c
           uint8_t* d = dst + h * sub_bytes;
           if (g.npair == 1) {
             load_slab(pm, g, 0, &full[stage], d, row + h * kRowsStage, 0);
+          } else if (g.split) {
+            // blocks (0,0) and (0,1): block h of slab 0 from CTA h to both; slab 1
+            // only to CTA 1, which loads it itself
+            if (pair == h)
+              load_slab(pm, g, 0, &full[stage], d, row + h * kRowsStage, (uint16_t)0x3);
+            if (pair == 1)
+              load_slab(pm, g, 1, &full[stage], d + kSlab * 128, row + h * kRowsStage, 0);
           } else {
             // block h of slab 0: CTA h (h = 0: (0,0), h = 1: (0,1)); of slab 1:
             // CTA 2 - h (h = 0: (1,1), h = 1: (0,1))
@@ -544,8 +552,9 @@ __global__ void tc_gram_sum_kernel(const double* __restrict__ partial, int64_t n
 // G (n x n, logical columns [U (kc) | A (B)]) from Ssum; H = S G S.  A mode
 // column of U appears twice in the padded panel (hi and lo plane); its Gram
 // entries are the sums over both.
-__global__ void tc_gram_assemble_kernel(const double* __restrict__ Ssum, GramGeom g, int kc, int B,
-                                        const double* __restrict__ D, double ff,
+__global__ void tc_gram_assemble_kernel(const double* __restrict__ Ssum,
+                                        const double* __restrict__ AAsum, GramGeom g, int kc,
+                                        int B, const double* __restrict__ D, double ff,
                                         double* __restrict__ G, double* __restrict__ H,
                                         int* __restrict__ status) {
   const int n = kc + B;
@@ -562,6 +571,11 @@ __global__ void tc_gram_assemble_kernel(const double* __restrict__ Ssum, GramGeo
       // each block holds its entries for x <= y (a diagonal block only those)
       const int x = min(ci[a], cj[b]), y = max(ci[a], cj[b]);
       const int sx = x / kSlab, sy = y / kSlab;
+      if (g.split && sx == 1) {
+        // block (1,1) = A^T A, summed by its own launch
+        s += AAsum[(size_t)(x % kSlab) * kSlab + (y % kSlab)];
+        continue;
+      }
       const int p = sx * g.nslab - sx * (sx - 1) / 2 + (sy - sx);
       s += Ssum[((size_t)p * kSlab + (x % kSlab)) * kSlab + (y % kSlab)];
     }
@@ -837,7 +851,7 @@ bool make_map_lines(CUtensorMap* m, const void* ptr, int64_t nlines, int box_lin
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-GramGeom gram_geom(int64_t M, int kc, int B, int max_clusters, int Kp) {
+GramGeom gram_geom(int64_t M, int kc, int B, int max_clusters, int Kp, bool split = false) {
   GramGeom g;
   g.M = M;
   g.Kp = Kp;
@@ -845,7 +859,8 @@ GramGeom gram_geom(int64_t M, int kc, int B, int max_clusters, int Kp) {
   g.Bp = (B + 7) & ~7;
   g.np = 2 * g.kcp + g.Bp;
   g.nslab = (int)ceil_div(g.np, kSlab);
-  g.npair = g.nslab * (g.nslab + 1) / 2;
+  g.split = split ? 1 : 0;
+  g.npair = split ? 2 : g.nslab * (g.nslab + 1) / 2;
   // every cluster resident at once; the clusters interleave slot by slot, so that
   // the CTAs in flight read neighbouring rows of every column
   g.nslot = ceil_div(M, (int64_t)kGramSubs * kRowsStage);
@@ -925,14 +940,56 @@ int gram_clusters(int kc, int B, int num_sms, const TcTune& tune) {
 }
 }  // namespace
 
+bool tc_gram_can_split(int kc, int B) {
+  return 2 * ((kc + 7) & ~7) == kSlab && B >= 1 && ((B + 7) & ~7) <= kSlab;
+}
+
+namespace {
+// Geometry of one Gram launch: split mode (blocks (0,0) and (0,1) in clusters of
+// two) takes the resident maximum of such clusters; at most `clusters` > 0 of the
+// others when given, else the tuned count.
+GramGeom launch_geom(int64_t M, int kc, int B, int num_sms, const TcTune& tune, int Kp, bool split,
+                     int clusters) {
+  if (split) return gram_geom(M, kc, B, gram_max_clusters(2, num_sms), Kp, true);
+  int c = gram_clusters(kc, B, num_sms, tune);
+  if (clusters > 0 && clusters < c) c = clusters;
+  return gram_geom(M, kc, B, c, Kp);
+}
+
+int gram_launch(const __nv_bfloat16* Ut, int Kp, int kc, const void* A, int64_t lda, int B,
+                const GramGeom& g, double** partial, int64_t* partial_cap, int* status,
+                cudaStream_t st);
+}  // namespace
+
 int tc_gram(const __nv_bfloat16* Ut, int Kp, int kc, const void* A, int64_t lda, int B, int dtype,
-            int64_t M, int num_sms, const TcTune& tune, double** partial, int64_t* partial_cap,
-            int* status, cudaStream_t st) {
+            int64_t M, int num_sms, const TcTune& tune, bool split, double** partial,
+            int64_t* partial_cap, int* status, cudaStream_t st) {
   if (dtype != PSVD_BF16) return PSVD_ERR_UNSUPPORTED;
   const int np = 2 * ((kc + 7) & ~7) + ((B + 7) & ~7);
   if (np > 256 || M > 0x7fffffffll - 256) return PSVD_ERR_SHAPE;
   if (kc > Kp) return PSVD_ERR_SHAPE;
-  GramGeom g = gram_geom(M, kc, B, gram_clusters(kc, B, num_sms, tune), Kp);
+  if (split && !tc_gram_can_split(kc, B)) return PSVD_ERR_SHAPE;
+  const GramGeom g = launch_geom(M, kc, B, num_sms, tune, Kp, split, 0);
+  return gram_launch(Ut, Kp, kc, A, lda, B, g, partial, partial_cap, status, st);
+}
+
+int tc_gram_aa(const void* A, int64_t lda, int B, int64_t M, int num_sms, int clusters,
+               double** partial, int64_t* partial_cap, double* AAsum, int* status,
+               cudaStream_t st) {
+  if (B < 1 || B > kSlab || M > 0x7fffffffll - 256) return PSVD_ERR_SHAPE;
+  TcTune none;
+  const GramGeom g = launch_geom(M, 0, B, num_sms, none, 0, false, clusters);
+  if (int rc = gram_launch(nullptr, 0, 0, A, lda, B, g, partial, partial_cap, status, st)) return rc;
+  tc_gram_sum_kernel<<<(unsigned)ceil_div((int64_t)kSlab * kSlab, 256), 256, 0, st>>>(*partial,
+                                                                                  g.nrange, 1, AAsum);
+  return cudaGetLastError() == cudaSuccess ? PSVD_OK : PSVD_ERR_CUDA;
+}
+
+namespace {
+int gram_launch(const __nv_bfloat16* Ut, int Kp, int kc, const void* A, int64_t lda, int B,
+                const GramGeom& g, double** partial, int64_t* partial_cap, int* status,
+                cudaStream_t st) {
+  const int64_t M = g.M;
   PanelMaps pm;
   const int64_t nlines = ceil_div(M, (int64_t)128) * 4 * Kp;
   for (int wi = 0; wi < 4; ++wi) {
@@ -986,11 +1043,12 @@ int tc_gram(const __nv_bfloat16* Ut, int Kp, int kc, const void* A, int64_t lda,
   }
   return PSVD_OK;
 }
+}  // namespace
 
 cudaError_t tc_gram_reduce(const double* partial, int64_t M, int kc, int B, int num_sms,
-                           const TcTune& tune, double ff, const double* D, double* G, double* H,
-                           int* status, cudaStream_t st) {
-  GramGeom g = gram_geom(M, kc, B, gram_clusters(kc, B, num_sms, tune), 0);
+                           const TcTune& tune, const double* AAsum, double ff, const double* D,
+                           double* G, double* H, int* status, cudaStream_t st) {
+  const GramGeom g = launch_geom(M, kc, B, num_sms, tune, 0, AAsum != nullptr, 0);
   const int64_t per = (int64_t)g.npair * kSlab * kSlab;
   double* Ssum = const_cast<double*>(partial) + g.nrange * per;
   tc_gram_sum_kernel<<<(unsigned)ceil_div(per, 256), 256, 0, st>>>(partial, g.nrange, g.npair, Ssum);
@@ -998,8 +1056,8 @@ cudaError_t tc_gram_reduce(const double* partial, int64_t M, int kc, int B, int 
   if (e != cudaSuccess) return e;
   const int n = kc + B;
   const int64_t tot = (int64_t)n * n;
-  tc_gram_assemble_kernel<<<(unsigned)ceil_div(tot, 256), 256, 0, st>>>(Ssum, g, kc, B, D, ff, G, H,
-                                                                        status);
+  tc_gram_assemble_kernel<<<(unsigned)ceil_div(tot, 256), 256, 0, st>>>(Ssum, AAsum, g, kc, B, D, ff,
+                                                                        G, H, status);
   return cudaGetLastError();
 }
 

@@ -35,13 +35,25 @@ int tc_update_max_stages(int kc, int B, int k1);
 // Partial Grams of the panel [Uh | Ul | A] (BF16; U = Uh + Ul, tiled as above with
 // column stride Kp) over row slots, written to *partial (grown if needed).  A
 // timed-out wait ORs 8 into *status.  Returns a PSVD status.
+// split: only the blocks [Uh | Ul]^T [Uh | Ul] and [Uh | Ul]^T A, in clusters of two
+// CTAs (tc_gram_can_split), the block A^T A coming from tc_gram_aa.
 int tc_gram(const __nv_bfloat16* Ut, int Kp, int kc, const void* A, int64_t lda, int B, int dtype,
-            int64_t M, int num_sms, const TcTune& tune, double** partial, int64_t* partial_cap,
-            int* status, cudaStream_t st);
+            int64_t M, int num_sms, const TcTune& tune, bool split, double** partial,
+            int64_t* partial_cap, int* status, cudaStream_t st);
+// Whether the panel of kc modes and B snapshots splits as [Uh | Ul] (one 128-column
+// slab) and A (a second one).
+bool tc_gram_can_split(int kc, int B);
+// A^T A (128 x 128 FP64, entries x <= y, ld 128) of a BF16 batch into AAsum, with at
+// most `clusters` CTAs (0 = as many as are resident), partials in *partial (grown
+// if needed).  Returns a PSVD status.
+int tc_gram_aa(const void* A, int64_t lda, int B, int64_t M, int num_sms, int clusters,
+               double** partial, int64_t* partial_cap, double* AAsum, int* status,
+               cudaStream_t st);
 // G = fixed-order FP64 sum of the partials (U^T U from the hi/lo blocks), H = S G S.
+// AAsum != null: the partials are those of a split Gram and A^T A is AAsum.
 cudaError_t tc_gram_reduce(const double* partial, int64_t M, int kc, int B, int num_sms,
-                           const TcTune& tune, double ff, const double* D, double* G, double* H,
-                           int* status, cudaStream_t st);
+                           const TcTune& tune, const double* AAsum, double ff, const double* D,
+                           double* G, double* H, int* status, cudaStream_t st);
 // BF16 elements of the packed update coefficients for K modes and batches <= maxB.
 size_t tc_t3_elems(int K, int maxB);
 // Ut_new = [Uh | Ul | A] * T on the tensor cores (modes tiled, column stride Kp):
