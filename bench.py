@@ -209,12 +209,13 @@ def run_e2e(psvd, batches, precision, steps, stream):
             "single_calls_value": steps * BATCH / dt1}
 
 
-# DRAM traffic of tc_gram_kernel from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum) of the current kernel on the M = 524,288 (256 x 2048
-# grid) case of this workload: reads scale with the rows, the partial-block
-# writes do not.
-TC_GRAM_READ_BYTES_PER_ROW = 269056768 / 524288
-TC_GRAM_WRITE_BYTES = 4101120
+# DRAM traffic of tc_gram_kernel in its split form (the steady-state Gram of
+# psvd_incorporate_batches) from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) on the M = 524,288 (256 x 2048 grid) case of this
+# workload: reads scale with the rows, the partial-block writes (76 clusters at
+# either size) do not.
+TC_GRAM_READ_BYTES_PER_ROW = 269622784 / 524288
+TC_GRAM_WRITE_BYTES = 4189184
 
 
 def roofline(res, precision, hbm_peak, peak_kind):
