@@ -127,3 +127,24 @@ def test_randomized_bad_config(p, q):
     with pytest.raises(psvd.PsvdError) as ei:
         psvd.psvd_create(4096, 8, 16, 1.0, psvd.PSVD_PREC_FP32, 1, p, q, 0)
     assert ei.value.status == psvd.PSVD_ERR_INVALID_ARG
+
+
+def test_randomized_tensor_core_batches_lookahead():
+    # psvd_incorporate_batches on a randomized tensor-core handle with resident
+    # batches (K = 64, so the A^T A look-ahead runs): the same sketches as the
+    # oracle's, the H of each step assembled from the split Gram and the look-ahead
+    gen = synthetic.TravellingWaves(128, 256, 256, 1.2, 1e-4, seed=1238)
+    bs = [synthetic.to_storage(gen.batch(i, 96), torch.bfloat16) for i in range(4)]
+    M = bs[0].shape[0]
+    s = psvd.StreamingSVD(M, 64, 96, 0.95, psvd.PSVD_PREC_BF16_TC, low_rank=1, oversample=10,
+                          power_iters=1, seed=7)
+    try:
+        s.initialize(bs[0].cuda())
+        s.incorporate_batches([b.cuda() for b in bs[1:]])
+        U = s.modes().cpu().double().numpy()
+        D = s.singular_values().cpu().numpy()
+        assert psvd.psvd_last_info(s.h)[0] >= 0
+    finally:
+        s.close()
+    Uo, Do = _oracle_rsvd(bs, 64, 0.95, 10, 1, seed=7)
+    _compare(U, D, Uo, Do, sig_tol=1e-4, ang_tol=1e-3, unit=U17, gram_res=160e-9)
