@@ -59,6 +59,10 @@ constexpr int kFoldStages = 1;
 // their float-float sums in registers).  Eighteen warps cap the registers at 112
 // per thread.
 constexpr int kGramEpiWarp0 = 2;
+// TMEM accumulators of a Gram CTA (128 columns each, 512 allocated): the MMA warp
+// fills one while the draining warps fold the others, so a fold's latency is hidden
+// as long as it is shorter than (kGramAcc - 1) slots of MMAs.
+constexpr int kGramAcc = 3;
 constexpr int kGramEpiWarps = 16;
 constexpr int kGramThreads = (kGramEpiWarp0 + kGramEpiWarps) * 32;
 constexpr int kUpdRows = 128;             // rows per update tile (UMMA M)
@@ -214,12 +218,35 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 // Fast2Sum fold (Dekker): hi + lo accumulates x, lo collecting the rounding error of
 // hi + x.  The error term is exact when |hi| >= |x|, which holds for a running Gram
 // total once its first chains are in (one 128-row chain is small next to the sum);
-// otherwise at most one rounding of the sum is lost.
-__device__ __forceinline__ void fold(float& hi, float& lo, float x) {
-  const float s = __fadd_rn(hi, x);
-  const float z = __fsub_rn(s, hi);
-  lo = __fadd_rn(lo, __fsub_rn(x, z));
+// otherwise at most one rounding of the sum is lost.  Done on packed FP32 pairs
+// (add/sub.rn.f32x2: each half rounded exactly as the scalar operation, half the
+// instructions).
+__device__ __forceinline__ uint64_t add_f32x2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t sub_f32x2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ void fold2(uint64_t& hi, uint64_t& lo, uint64_t x) {
+  const uint64_t s = add_f32x2(hi, x);
+  const uint64_t z = sub_f32x2(s, hi);
+  lo = add_f32x2(lo, sub_f32x2(x, z));
   hi = s;
+}
+__device__ __forceinline__ uint64_t pack_f32x2(uint32_t a, uint32_t b) {
+  uint64_t d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "r"(a), "r"(b));
+  return d;
+}
+__device__ __forceinline__ void unpack_f32x2(uint64_t v, float& a, float& b) {
+  uint32_t x, y;
+  asm("mov.b64 {%0, %1}, %2;" : "=r"(x), "=r"(y) : "l"(v));
+  a = __uint_as_float(x);
+  b = __uint_as_float(y);
 }
 
 // Shared-memory matrix descriptor, SWIZZLE_128B (layout type 2), version 1.
@@ -321,7 +348,7 @@ __device__ __forceinline__ void load_slab(const PanelMaps& pm, const GramGeom& g
 // A CTA's full barrier expects all bytes it receives; its empty barrier collects
 // the MMA commits of every CTA of the cluster, so no CTA's copy lands in a stage
 // that another CTA still reads.
-// TMEM: two FP32 accumulators (columns 0 and 128) alternate between the MMA warp
+// TMEM: kGramAcc FP32 accumulators (128 columns each) rotate between the MMA warp
 // and the epilogue, which folds each finished 128-row partial into a float-float
 // running sum held in the draining warps' registers.  The block is written as
 // FP64 (hi + lo) to partial[range][pair][128][128].
@@ -340,9 +367,9 @@ __global__ void __launch_bounds__(kGramThreads, 1) tc_gram_kernel(const __grid_c
   uint8_t* stages = base;
   uint64_t* full = (uint64_t*)(stages + (size_t)kGramStages * stage_bytes);
   uint64_t* empty = full + kGramStages;
-  uint64_t* acc_full = empty + kGramStages;  // [2]
-  uint64_t* acc_empty = acc_full + 2;        // [2]
-  uint64_t* mma_done = acc_empty + 2;
+  uint64_t* acc_full = empty + kGramStages;  // [kGramAcc]
+  uint64_t* acc_empty = acc_full + kGramAcc;  // [kGramAcc]
+  uint64_t* mma_done = acc_empty + kGramAcc;
   uint32_t* tmem_slot = (uint32_t*)(mma_done + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
@@ -359,7 +386,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) tc_gram_kernel(const __grid_c
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], g.npair);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kGramAcc; ++b) {
       mbar_init(&acc_full[b], 1);
       mbar_init(&acc_empty[b], kGramEpiWarps);
     }
@@ -441,9 +468,9 @@ __global__ void __launch_bounds__(kGramThreads, 1) tc_gram_kernel(const __grid_c
       uint32_t phase = 0;
       int st = 0;
       for (int f = 0; f < nfold; ++f) {
-        const int b = f & 1;
-        const uint32_t use = (uint32_t)((f >> 1) & 1);
-        if (f >= 2 && !mbar_wait(&acc_empty[b], use ^ 1, abort_flag, err)) break;
+        const int b = f % kGramAcc;
+        const uint32_t use = (uint32_t)((f / kGramAcc) & 1);
+        if (f >= kGramAcc && !mbar_wait(&acc_empty[b], use ^ 1, abort_flag, err)) break;
         const uint32_t d_tmem = tmem_base + (uint32_t)(b * kSlab);
         bool ok = true;
         for (int k4 = 0; k4 < g.fold_stages && st < nst; ++k4, ++st) {
@@ -491,11 +518,11 @@ __global__ void __launch_bounds__(kGramThreads, 1) tc_gram_kernel(const __grid_c
     const uint32_t lane_base = tmem_base + ((uint32_t)(q * 32) << 16);
     const int c0 = 32 * ch;
     const bool need = c0 < w && (!diag || c0 + 32 > 32 * q);
-    float hi[32], lo[32];
+    uint64_t hi[16], lo[16];  // columns c0 + 2i, c0 + 2i + 1 packed
     bool ok = true;
     for (int f = 0; f < nfold; ++f) {
-      const int b = f & 1;
-      const uint32_t use = (uint32_t)((f >> 1) & 1);
+      const int b = f % kGramAcc;
+      const uint32_t use = (uint32_t)((f / kGramAcc) & 1);
       if (!mbar_wait(&acc_full[b], use, abort_flag, err)) {
         ok = false;
         break;
@@ -509,13 +536,13 @@ __global__ void __launch_bounds__(kGramThreads, 1) tc_gram_kernel(const __grid_c
           tmem_ld16_nowait(lane_base + (uint32_t)(b * kSlab + c0 + 16 * p), a);
           tmem_wait_ld();
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const float x = __uint_as_float(a[i]);
+          for (int i = 0; i < 8; ++i) {
+            const uint64_t x = pack_f32x2(a[2 * i], a[2 * i + 1]);
             if (f == 0) {
-              hi[16 * p + i] = x;
-              lo[16 * p + i] = 0.f;
+              hi[8 * p + i] = x;
+              lo[8 * p + i] = 0ull;
             } else {
-              fold(hi[16 * p + i], lo[16 * p + i], x);
+              fold2(hi[8 * p + i], lo[8 * p + i], x);
             }
           }
         }
@@ -528,7 +555,13 @@ __global__ void __launch_bounds__(kGramThreads, 1) tc_gram_kernel(const __grid_c
       const int row_in_slab = q * 32 + lane;
       double* orow = partial + (((size_t)range * g.npair + pair) * kSlab + row_in_slab) * kSlab;
 #pragma unroll
-      for (int i = 0; i < 32; ++i) orow[c0 + i] = (double)hi[i] + (double)lo[i];
+      for (int i = 0; i < 16; ++i) {
+        float h0, h1, l0, l1;
+        unpack_f32x2(hi[i], h0, h1);
+        unpack_f32x2(lo[i], l0, l1);
+        orow[c0 + 2 * i] = (double)h0 + (double)l0;
+        orow[c0 + 2 * i + 1] = (double)h1 + (double)l1;
+      }
     }
   }
   tc_fence_before();
