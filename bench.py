@@ -214,8 +214,8 @@ def run_e2e(psvd, batches, precision, steps, stream):
 # dram__bytes_write.sum) on the M = 524,288 (256 x 2048 grid) case of this
 # workload: reads scale with the rows, the partial-block writes (76 clusters at
 # either size) do not.
-TC_GRAM_READ_BYTES_PER_ROW = 269622784 / 524288
-TC_GRAM_WRITE_BYTES = 4189184
+TC_GRAM_READ_BYTES_PER_ROW = 268602624 / 524288
+TC_GRAM_WRITE_BYTES = 3468800
 
 
 def roofline(res, precision, hbm_peak, peak_kind):
