@@ -6,6 +6,7 @@ Philox4x64), chosen so that a plausible slip -- a dropped term, a wrong sign or
 index, a transposed operand, a wrong truncation or ordering -- fails at least one.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -290,6 +291,27 @@ def test_philox4x64_matches_numpy_bit_generator(ctr, key):
             c1[1] = (c1[1] + 1) % 2 ** 64
         out += oracle.philox4x64(c1, key)
     assert out == raw
+
+
+def _philox_kat():
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox_kat.txt")
+    rows = []
+    for line in open(path):
+        f = line.split()
+        if not f or f[0].startswith("#"):
+            continue
+        w = [int(x, 16) for x in f[2:]]
+        rows.append((f[0], int(f[1]), w[0:4], w[4:6], w[6:10]))
+    return rows
+
+
+@pytest.mark.parametrize("gen,rounds,ctr,key,expect", _philox_kat())
+def test_philox_published_known_answers(gen, rounds, ctr, key, expect):
+    # the published known-answer vectors of Philox4x32-10 (the generator of the
+    # Gaussian test matrix) and Philox4x64-10: a mistyped multiplier, Weyl constant
+    # or word order changes every output word
+    f = oracle.philox4x32 if gen == "philox4x32" else oracle.philox4x64
+    assert list(f(ctr, key, rounds)) == expect
 
 
 def test_philox4x32_bit_statistics_and_avalanche():
