@@ -137,11 +137,19 @@ int psvd_incorporate_data(psvd_handle h, const void* A, int64_t lda, int32_t B, 
 
 /* psvd_incorporate_batches: psvd_incorporate_data on `count` batches in order,
  * A[0], ..., A[count-1] (host array of pointers; each batch M x B with leading
- * dimension lda and the given dtype, device or host memory), with the same result
- * as the count single calls.  Host batches are copied to the device on a copy
- * stream of the handle into two alternating staging buffers, so the copy of batch
- * i+1 runs while batch i is processed (pinned host memory makes the copies
- * asynchronous; pageable memory still works, with less overlap).  s_out (may be
+ * dimension lda and the given dtype, device or host memory).  Host batches are
+ * copied to the device on a copy stream of the handle into two alternating staging
+ * buffers, so the copy of batch i+1 runs while batch i is processed (pinned host
+ * memory makes the copies asynchronous; pageable memory still works, with less
+ * overlap); the result is then bit for bit that of the count single calls, as on
+ * the FP32 and FP64 paths.  On the tensor-core path, when batch i+1 is in device
+ * memory (16-byte aligned base and lda * 2) and the panel splits as one mode slab
+ * and one snapshot slab (2 * roundup(K, 8) == 128, B <= 128), its A^T A block is
+ * summed on a side stream of the handle while batch i's small solve runs and its
+ * Gram computes only the blocks with the modes: the same Gram in another
+ * summation order, so the result agrees with the single calls to rounding, not
+ * bit for bit.  Every side-stream launch is joined back into the handle's stream
+ * before the call's last batch is done.  s_out (may be
  * null; host or device, FP64, count x K with leading dimension K) receives each
  * batch's singular values (the current mode count of them, descending) as soon as
  * that batch is done.  Returns after enqueuing; the caller keeps every batch and

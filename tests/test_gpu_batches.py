@@ -103,3 +103,45 @@ def test_tensor_core_lookahead_matches_single_calls_and_oracle(ny, nx, B, nb):
     # each batch's singular values: the same as the single calls' at the path's bar
     for i, s in enumerate(sig1):
         assert np.allclose(sig2[i, :len(s)], s, rtol=1e-4, atol=1e-4 * s[0])
+
+
+def test_mixed_host_and_device_batches():
+    # host (pinned and pageable) and device batches in one call: the look-ahead runs
+    # only ahead of device batches; every batch still lands as with single calls
+    gen = synthetic.TravellingWaves(128, 256, 256, 1.2, 1e-4, seed=77)
+    bs = [synthetic.to_storage(gen.batch(i, 128), torch.bfloat16) for i in range(6)]
+    TC = psvd.PSVD_PREC_BF16_TC
+    U1, D1, _ = _run_single(bs, 64, 0.95, TC)
+    M = bs[0].shape[0]
+    s = psvd.StreamingSVD(M, 64, 128, 0.95, TC)
+    try:
+        s.initialize(bs[0].cuda())
+        mixed = [bs[1].pin_memory(), bs[2].cuda(), bs[3].clone(), bs[4].cuda(), bs[5].cuda()]
+        s_out = torch.zeros((5, 64), dtype=torch.float64).pin_memory()
+        s.incorporate_batches(mixed, s_out)
+        U2, D2 = s.modes().cpu().numpy(), s.singular_values().cpu().numpy()
+    finally:
+        s.close()
+    unit = 2.0 ** -17
+    _compare(U2.astype(np.float64), D2, U1.astype(np.float64), D1, sig_tol=1e-4, ang_tol=1e-3,
+             unit=unit, gram_res=2e-9)
+    assert np.array_equal(s_out.numpy()[4], D2)
+    Uo, Do, s_next = _oracle_run_gap(bs, 64, 0.95)
+    _compare(U2.astype(np.float64), D2, Uo, Do, sig_tol=1e-4, ang_tol=1e-3, unit=unit,
+             s_next=s_next)
+
+
+def test_single_batch_and_pageable_numpy_fp32():
+    # count = 1, and pageable numpy batches on the FP32 path: bit for bit the single calls
+    gen = synthetic.TravellingWaves(64, 128, 64, 1.5, 1e-3, seed=78)
+    bs = [synthetic.to_storage(gen.batch(i, 32), torch.float32) for i in range(4)]
+    U1, D1, _ = _run_single(bs, 16, 0.9, psvd.PSVD_PREC_FP32)
+    s = psvd.StreamingSVD(bs[0].shape[0], 16, 32, 0.9, psvd.PSVD_PREC_FP32)
+    try:
+        s.initialize(bs[0].cuda())
+        s.incorporate_batches([np.asfortranarray(bs[1].numpy())])
+        s.incorporate_batches([np.asfortranarray(b.numpy()) for b in bs[2:]])
+        U2, D2 = s.modes().cpu().numpy(), s.singular_values().cpu().numpy()
+    finally:
+        s.close()
+    assert np.array_equal(U1, U2) and np.array_equal(D1, D2)
