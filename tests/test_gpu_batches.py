@@ -84,7 +84,7 @@ def test_batches_reject_mismatched_shapes():
 
 
 @pytest.mark.parametrize("ny,nx,B,nb", [
-    (128, 256, 128, 5),   # the config-3 panel shape: [Uh | Ul] and A one slab each
+    (128, 256, 128, 5),   # K = 64, B = 128: [Uh | Ul] and A one slab each
     (125, 256, 100, 5),   # ragged last row tile, B not a multiple of 16
     (96, 128, 40, 6),     # k grows 40 -> 64: the split starts at the third step
 ])
