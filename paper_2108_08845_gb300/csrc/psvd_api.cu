@@ -586,6 +586,7 @@ int psvd_incorporate_data(psvd_handle h, const void* A, int64_t lda, int32_t B, 
   if (!h) return PSVD_ERR_INVALID_ARG;
   if (h->kc == 0) return PSVD_ERR_NOT_INITIALIZED;
   if (int rc = check_batch(h, A, lda, B, dtype)) return rc;
+  h->aa_iter = -1;  // a look-ahead left by a failed batches call is never used
   const void* Ad;
   int64_t ldd;
   if (int rc = stage_input(h, A, lda, h->M, B, dtype, use_tc(h), &Ad, &ldd)) return rc;
@@ -596,6 +597,9 @@ int psvd_incorporate_batches(psvd_handle h, const void* const* A, int32_t count,
                              int32_t B, int32_t dtype, double* s_out) {
   if (!h || !A || count < 1) return PSVD_ERR_INVALID_ARG;
   if (h->kc == 0) return PSVD_ERR_NOT_INITIALIZED;
+  // a look-ahead is made and used within one call: none survives from an earlier one
+  // (its batch buffer may hold other data by now)
+  h->aa_iter = -1;
   // every batch is checked before the first one is enqueued
   for (int i = 0; i < count; ++i)
     if (int rc = check_batch(h, A[i], lda, B, dtype)) return rc;
