@@ -83,21 +83,23 @@ def test_batches_reject_mismatched_shapes():
         s.close()
 
 
-@pytest.mark.parametrize("ny,nx,B,nb", [
-    (128, 256, 128, 5),   # K = 64, B = 128: [Uh | Ul] and A one slab each
-    (125, 256, 100, 5),   # ragged last row tile, B not a multiple of 16
-    (96, 128, 40, 6),     # k grows 40 -> 64: the split starts at the third step
+@pytest.mark.parametrize("ny,nx,B,nb,K", [
+    (128, 256, 128, 5, 64),   # K = 64, B = 128: [Uh | Ul] and A one slab each
+    (125, 256, 100, 5, 64),   # ragged last row tile, B not a multiple of 16
+    (96, 128, 40, 6, 64),     # k grows 40 -> 64: the split starts at the third step
+    (96, 128, 100, 4, 57),    # K = 57: mode planes padded to 64 columns
+    (64, 128, 8, 12, 60),     # a one-box snapshot slab (B = 8)
 ])
-def test_tensor_core_lookahead_matches_single_calls_and_oracle(ny, nx, B, nb):
+def test_tensor_core_lookahead_matches_single_calls_and_oracle(ny, nx, B, nb, K):
     gen = synthetic.TravellingWaves(ny, nx, 256, 1.2, 1e-4, seed=ny + B)
     bs = [synthetic.to_storage(gen.batch(i, B), torch.bfloat16) for i in range(nb)]
     TC = psvd.PSVD_PREC_BF16_TC
-    U1, D1, sig1 = _run_single(bs, 64, 0.95, TC)
-    U2, D2, sig2 = _run_batched(bs, 64, 0.95, TC, host=False)
+    U1, D1, sig1 = _run_single(bs, K, 0.95, TC)
+    U2, D2, sig2 = _run_batched(bs, K, 0.95, TC, host=False)
     unit = 2.0 ** -17
     _compare(U2.astype(np.float64), D2, U1.astype(np.float64), D1, sig_tol=1e-4, ang_tol=1e-3,
              unit=unit, gram_res=2e-9)
-    Uo, Do, s_next = _oracle_run_gap(bs, 64, 0.95)
+    Uo, Do, s_next = _oracle_run_gap(bs, K, 0.95)
     _compare(U2.astype(np.float64), D2, Uo, Do, sig_tol=1e-4, ang_tol=1e-3, unit=unit,
              s_next=s_next)
     # each batch's singular values: the same as the single calls' at the path's bar
