@@ -133,7 +133,7 @@ def make_batches(device, count: int):
     return out
 
 
-def run_arm(psvd, batches, precision, steps, warmup, stream, sampler=None):
+def run_arm(psvd, batches, precision, steps, warmup, stream, sampler=None, autotune=True):
     """Times `steps` updates after initialise + warm-up; returns a result dict."""
     import torch
 
@@ -141,7 +141,9 @@ def run_arm(psvd, batches, precision, steps, warmup, stream, sampler=None):
     try:
         nb = len(batches)
         psvd.psvd_initialize(h, batches[0])
-        tune = list(psvd.psvd_autotune(h, batches[1]))  # launch shapes for this panel
+        # launch shapes for this panel (the defaults with --no-autotune: a profiled
+        # run's timings, distorted by the profiler, would pick other shapes)
+        tune = list(psvd.psvd_autotune(h, batches[1])) if autotune else None
         if warmup > 0:
             psvd.psvd_incorporate_batches(h, [batches[1 + i % (nb - 1)] for i in range(warmup)])
         psvd.psvd_set_profiling(h, True)
@@ -169,7 +171,7 @@ def run_arm(psvd, batches, precision, steps, warmup, stream, sampler=None):
             "autotune": tune}
 
 
-def run_e2e(psvd, batches, precision, steps, stream):
+def run_e2e(psvd, batches, precision, steps, stream, autotune=True):
     """Same metric through the public API from pinned host inputs: one
     psvd_incorporate_batches call over `steps` host batches (each batch's copy to
     the device overlaps the previous batch's update) that also reads every step's
@@ -187,7 +189,8 @@ def run_e2e(psvd, batches, precision, steps, stream):
     h = psvd.psvd_create(M_FULL, K_MODES, BATCH, FF, precision, stream=stream)
     try:
         psvd.psvd_initialize(h, batches[0])
-        psvd.psvd_autotune(h, batches[1])  # cached from the timed arm
+        if autotune:
+            psvd.psvd_autotune(h, batches[1])  # cached from the timed arm
         psvd.psvd_incorporate_batches(h, host[:2], s_host[:2], K_MODES)  # staging + copy stream
         psvd.psvd_get_singular_values(h, s_host[0])
         torch.cuda.synchronize()
@@ -553,6 +556,8 @@ def main():
     ap.add_argument("--precision", default="both", choices=["both", "fp32", "bf16_tc"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="default launch shapes (for profiler captures)")
     ap.add_argument("--e2e-steps", type=int, default=24)
     ap.add_argument("--ny", type=int, default=NY, help="grid rows (profiling on smaller grids)")
     ap.add_argument("--nx", type=int, default=NX, help="grid columns")
@@ -595,10 +600,11 @@ def main():
     results = {}
     for arm in arms:
         results[arm] = run_arm(psvd, batches, prec_code[arm], args.steps, args.warmup, stream,
-                               ClockSampler(0))
+                               ClockSampler(0), autotune=not args.no_autotune)
     head = arms[0]
     r = results[head]
-    e2e = (run_e2e(psvd, batches, prec_code[head], args.e2e_steps, stream) if args.e2e_steps > 0
+    e2e = (run_e2e(psvd, batches, prec_code[head], args.e2e_steps, stream,
+                   autotune=not args.no_autotune) if args.e2e_steps > 0
            else None)
     ms = r["ms"]
     value = args.steps * BATCH / (ms * 1e-3)
