@@ -286,7 +286,7 @@ int psvd_update_adjoint(psvd_handle h, int32_t kc, const float* U, int64_t ldu, 
  * is kept by the handle and cached for the process under the shape and SM count, so
  * later calls with the same shape take it without timing.
  *   FP32 handles (A PSVD_F32 or PSVD_BF16): Gram row chunks sized for 1, 2, 4 or
- *   8 resident CTAs per SM, and mode-update tiles of 64 or 128 rows; choice
+ *   8 resident CTAs per SM, and mode-update tiles of 64, 128 or 256 rows; choice
  *   receives {CTAs per SM, update tile rows, 0}.
  *   Tensor-core handles (A PSVD_BF16): the Gram's cluster count (the resident
  *   maximum, 2/3, 1/2 or 1/3 of it), the update's CTA count (one per SM or half

@@ -543,6 +543,8 @@ cudaError_t update_simt_launch(const PanelF32& p, const float* T, int k1, float*
                                cudaStream_t st, int tile_rows) {
   if (tile_rows == 64)
     launch_update_cols<2>(p, T, k1, Unew, ldo, st);
+  else if (tile_rows == 256)
+    launch_update_cols<8>(p, T, k1, Unew, ldo, st);
   else
     launch_update_cols<4>(p, T, k1, Unew, ldo, st);
   return cudaGetLastError();

@@ -1215,7 +1215,7 @@ int psvd_autotune(psvd_handle h, const void* A, int64_t lda, int32_t B, int32_t 
     }
   }
   best_ms = 1e30f;
-  static const int kRows[] = {64, 128};
+  static const int kRows[] = {64, 128, 256};
   for (int rows : kRows) {
     float ms = 0.f;
     int rc = time_ms(h->st, 3, [&]() -> int {

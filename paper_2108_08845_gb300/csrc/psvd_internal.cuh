@@ -70,7 +70,7 @@ cudaError_t gram_reduce_launch(const double* partial, int nchunk, int n, int kc,
                                const double* D, double ff, double* G, double* H, int* info,
                                cudaStream_t st);
 // Unew (M x k1, ldo) = [U | A] * T (n x k1, FP32, ldt = n), in tiles of tile_rows
-// (64 or 128) rows by the narrowest of 16, 32 or 64 columns covering k1.
+// (64, 128 or 256) rows by the narrowest of 16, 32 or 64 columns covering k1.
 cudaError_t update_simt_launch(const PanelF32& p, const float* T, int k1, float* Unew,
                                int64_t ldo, cudaStream_t st, int tile_rows = 128);
 

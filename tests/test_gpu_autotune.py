@@ -26,7 +26,7 @@ def test_autotune_choice_cache_state_and_parity():
     s.initialize(dev[0])
     U0, D0 = s.modes().cpu().numpy(), s.singular_values().cpu().numpy()
     cps, rows = psvd.psvd_autotune(s.h, dev[1])
-    assert cps in (1, 2, 4, 8) and rows in (64, 128)
+    assert cps in (1, 2, 4, 8) and rows in (64, 128, 256)
     # the trials leave the modes, singular values and status as they were
     assert np.array_equal(s.modes().cpu().numpy(), U0)
     assert np.array_equal(s.singular_values().cpu().numpy(), D0)
