@@ -127,3 +127,31 @@ def test_256_mode_waves_2p21_rows(waves256_grid1024x2048, precision, sig_tol, an
     bs, Uo, Do, s_next = waves256_grid1024x2048
     U, D, _ = _gpu_run(bs, K=64, ff=0.95, precision=precision)
     _compare(U, D, Uo, Do, sig_tol=sig_tol, ang_tol=ang_tol, unit=unit, s_next=s_next)
+
+
+def test_tc_save_load_resumes_bit_identically(tmp_path):
+    # the hi/lo mode planes go to the checkpoint and come back exactly: a loaded
+    # handle continues (with the A^T A look-ahead of the batches call) bit for bit
+    gen = synthetic.TravellingWaves(96, 128, 256, 1.2, 1e-4, seed=1240)
+    bs = [synthetic.to_storage(gen.batch(i, 128), torch.bfloat16).cuda() for i in range(6)]
+    M = bs[0].shape[0]
+    s = psvd.StreamingSVD(M, 64, 128, 0.95, TC)
+    h2 = None
+    try:
+        s.initialize(bs[0])
+        s.incorporate_data(bs[1])
+        path = str(tmp_path / "tc_state.psvd")
+        psvd.psvd_save(s.h, path)
+        h2 = psvd.psvd_load(path)
+        s.incorporate_batches(bs[2:])
+        psvd.psvd_incorporate_batches(h2, bs[2:])
+        U1, s1 = s.modes(), s.singular_values()
+        U2 = torch.empty_like(U1.T).T
+        psvd.psvd_get_modes(h2, U2)
+        s2 = torch.empty_like(s1)
+        psvd.psvd_get_singular_values(h2, s2)
+        assert torch.equal(U1, U2) and torch.equal(s1, s2)
+    finally:
+        if h2:
+            psvd.psvd_destroy(h2)
+        s.close()
