@@ -17,21 +17,22 @@ from tests.test_gpu_fp32 import _compare
 pytestmark = pytest.mark.gpu
 
 
-def _streams(count, M, B, T, seed):
-    """count independent streams, T batches each (column-major FP32 on the host)."""
+def _streams(count, M, B, T, seed, dtype=torch.float32):
+    """count independent streams, T batches each (column-major on the host)."""
     out = []
     for i in range(count):
         A, *_ = synthetic.low_rank(M, B * T, 24, 1e-6, seed + 17 * i)
-        A = synthetic.to_storage(A, torch.float32)
+        A = synthetic.to_storage(A, dtype)
         out.append([A[:, t * B:(t + 1) * B] for t in range(T)])
     return out
 
 
-def _run_group(streams, M, K, B, ff):
+def _run_group(streams, M, K, B, ff, prec=psvd.PSVD_PREC_FP32):
     count, T = len(streams), len(streams[0])
-    g = psvd.psvd_group_create(count, M, K, B, ff, psvd.PSVD_PREC_FP32)
+    g = psvd.psvd_group_create(count, M, K, B, ff, prec)
     # a ring of two input buffers per member: later calls repeat the pointers
-    ring = [[torch.empty(B, M, dtype=torch.float32, device="cuda").T for _ in range(count)]
+    dt = streams[0][0].dtype
+    ring = [[torch.empty(B, M, dtype=dt, device="cuda").T for _ in range(count)]
             for _ in range(2)]
     for t in range(T):
         buf = ring[t % 2]
@@ -56,8 +57,8 @@ def _run_group(streams, M, K, B, ff):
     return rc, stats, res
 
 
-def _run_single(batches, M, K, B, ff):
-    s = psvd.StreamingSVD(M, K, B, ff, psvd.PSVD_PREC_FP32)
+def _run_single(batches, M, K, B, ff, prec=psvd.PSVD_PREC_FP32):
+    s = psvd.StreamingSVD(M, K, B, ff, prec)
     s.initialize(batches[0].cuda())
     for A in batches[1:]:
         s.incorporate_data(A.cuda())
@@ -81,3 +82,19 @@ def test_group_matches_single_handles_and_replays(count, M, T):
     for i in (0, count - 1):
         Uo, Do = oracle.stream_run([b.double().numpy() for b in streams[i]], K, ff)
         _compare(res[i][0].astype(np.float64), res[i][1], Uo, Do)
+
+
+def test_tensor_core_group_matches_single_handles():
+    # tensor-core members run their launches directly on their own streams (no
+    # graph): still the same kernels on the same inputs as lone handles
+    count, M, T, K, B, ff = 6, 12288, 5, 16, 16, 0.95
+    TC = psvd.PSVD_PREC_BF16_TC
+    streams = _streams(count, M, B, T, seed=900, dtype=torch.bfloat16)
+    rc, _, res = _run_group(streams, M, K, B, ff, TC)
+    assert rc == psvd.PSVD_OK
+    for i in (0, count - 1):
+        U1, D1 = _run_single(streams[i], M, K, B, ff, TC)
+        assert np.array_equal(res[i][1], D1) and np.array_equal(res[i][0], U1)
+        Uo, Do = oracle.stream_run([b.double().numpy() for b in streams[i]], K, ff)
+        _compare(res[i][0].astype(np.float64), res[i][1], Uo, Do, sig_tol=1e-4, ang_tol=1e-3,
+                 unit=2.0 ** -17)
